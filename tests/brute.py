@@ -1,0 +1,128 @@
+"""Brute-force restatements of the formats, one bit at a time, for tiny inputs.
+
+These build the expected byte strings directly from the prose definitions
+(Python integers used as bit strings), with none of the word-level logic of
+Algorithm 1.  They exist to pin the oracle to something other than itself.
+"""
+from __future__ import annotations
+
+
+def bitstring_put(acc: int, pos: int, value: int, b: int) -> int:
+    for k in range(b):
+        if (value >> k) & 1:
+            acc |= 1 << (pos + k)
+    return acc
+
+
+def bits_of(v: int) -> int:
+    return v.bit_length()  # smallest b with v < 2**b
+
+
+def s4_block_words(deltas, b: int):
+    """Fig. 2: integer n -> lane n % 4, slot n // 4; each lane is an LSB-first
+    b-bit stream; lane word k is block word 4k + lane."""
+    lanes = [0, 0, 0, 0]
+    for n, v in enumerate(deltas):
+        lanes[n % 4] = bitstring_put(lanes[n % 4], b * (n // 4), v, b)
+    words = [0] * (4 * b)
+    for k in range(b):
+        for s in range(4):
+            words[4 * k + s] = (lanes[s] >> (32 * k)) & 0xFFFFFFFF
+    return words
+
+
+def gl_block_words(deltas, b: int):
+    """GL: delta of in-block position 4t+s at bit b*(32s+t)."""
+    acc = 0
+    for t in range(32):
+        for s in range(4):
+            acc = bitstring_put(acc, b * (32 * s + t), deltas[4 * t + s], b)
+    return [(acc >> (32 * k)) & 0xFFFFFFFF for k in range(4 * b)]
+
+
+def le32(words) -> bytes:
+    return b"".join(int(w).to_bytes(4, "little") for w in words)
+
+
+def varint(values) -> bytes:
+    out = bytearray()
+    for v in values:
+        while True:
+            if v < 128:
+                out.append(v | 128)
+                break
+            out.append(v & 127)
+            v >>= 7
+    return bytes(out)
+
+
+def pl_stream(x) -> bytes:
+    """The S4-BP128-D4 paper layout of Section 4.3 with our header/tail
+    reading, built from the prose: D4 deltas against (0,0,0,0), meta-blocks
+    of 16 widths + 16 blocks, leftover blocks with a width byte each, varint
+    of D1 gaps for the last n mod 128 integers."""
+    x = [int(v) for v in x]
+    n = len(x)
+    nb = n // 128
+    np_ = 128 * nb
+    d = [(x[i] - (x[i - 4] if i >= 4 else 0)) % 2**32 for i in range(np_)]
+    widths = [bits_of(max(d[128 * k:128 * k + 128])) for k in range(nb)]
+    body = bytearray()
+    for m in range(nb // 16):
+        ks = range(16 * m, 16 * m + 16)
+        body += bytes(widths[k] for k in ks)
+        for k in ks:
+            body += le32(s4_block_words(d[128 * k:128 * k + 128], widths[k]))
+    for k in range(16 * (nb // 16), nb):
+        body.append(widths[k])
+        body += le32(s4_block_words(d[128 * k:128 * k + 128], widths[k]))
+    prev = x[np_ - 1] if np_ else 0
+    gaps = []
+    for v in x[np_:]:
+        gaps.append((v - prev) % 2**32)
+        prev = v
+    tail = varint(gaps)
+    hdr = le32([n, 0, len(tail), 0])
+    return hdr + bytes(body) + tail
+
+
+def gl_stream(x) -> bytes:
+    """GL layout (ours): see the oracle header for the field list."""
+    x = [int(v) for v in x]
+    n = len(x)
+    nb = (n + 127) // 128
+    ns = (nb + 31) // 32
+
+    def up16(v):
+        return (v + 15) // 16 * 16
+
+    off_first = 64
+    off_sbo = off_first + up16(4 * nb)
+    off_bw = off_sbo + up16(4 * (ns + 1))
+    off_payload = off_bw + up16(nb)
+    first, widths, payload, sbo = [], [], [], []
+    for k in range(nb):
+        blk = x[128 * k:128 * k + 128]
+        F = blk[0]
+        full = list(blk)
+        for i in range(len(blk), 128):
+            full.append(full[i - 4] if i >= 4 else F)
+        d = [(full[i] - (full[i - 4] if i >= 4 else F)) % 2**32
+             for i in range(128)]
+        b = bits_of(max(d))
+        if k % 32 == 0:
+            sbo.append(len(payload))
+        first.append(F)
+        widths.append(b)
+        payload += gl_block_words(d, b)
+    sbo.append(len(payload))
+    total = off_payload + 4 * len(payload)
+    out = bytearray(total)
+    hdr = [0x344C4742, 1, n, nb, ns, len(payload), off_first, off_sbo, off_bw,
+           off_payload, total & 0xFFFFFFFF, total >> 32, 0, 0, 0, 0]
+    out[0:64] = le32(hdr)
+    out[off_first:off_first + 4 * nb] = le32(first)
+    out[off_sbo:off_sbo + 4 * (ns + 1)] = le32(sbo)
+    out[off_bw:off_bw + nb] = bytes(widths)
+    out[off_payload:] = le32(payload)
+    return bytes(out)
