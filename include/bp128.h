@@ -1,0 +1,155 @@
+/*
+ * bp128.h -- C ABI of the GB300 library for S4-BP128-D4 posting lists:
+ * decoding and conjunctive intersection (Lemire, Boytsov and Kurz, "SIMD
+ * Compression and the Intersection of Sorted Integers", arXiv 1401.6399).
+ *
+ * Problem statement (Section 1, Section 6): posting lists are sorted lists of
+ * distinct 32-bit document identifiers, stored compressed; the library takes
+ * compressed lists in and returns the decoded list, or the sorted
+ * intersection of several lists.  All arithmetic is exact 32-bit integer.
+ *
+ * Conventions for every call
+ *  - Host calls are synchronous and use caller-owned host buffers.
+ *  - Device calls take device pointers and a CUDA stream (cudaStream_t passed
+ *    as void*; NULL means the legacy default stream).  They only enqueue
+ *    work: they allocate no memory, never synchronise the stream, and return
+ *    once the kernels are queued.  The caller owns every buffer and must keep
+ *    it alive until the stream reaches that point.
+ *  - The return value reports argument errors and launch failures at once
+ *    (BP_ERR_ARG, BP_ERR_CUDA).  Errors found in the data (a corrupt stream,
+ *    a full output buffer, a wait that timed out) are written by the kernels
+ *    to *d_status, a device uint32 that the caller sets to BP_OK before the
+ *    first call and reads after synchronising; the first error recorded wins.
+ *    Several calls may share one status word.
+ *  - Scratch: calls that need temporary device memory take (d_scratch,
+ *    scratch_bytes); the matching *_scratch_bytes() function gives the
+ *    required size, and a smaller buffer returns BP_ERR_SCRATCH.  Scratch
+ *    needs no initialisation and its contents are undefined afterwards.
+ *  - Nothing here falls back to the CPU.
+ */
+#ifndef BP128_H
+#define BP128_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BP_OK = 0,
+  BP_ERR_ARG = 1,      /* invalid argument                                */
+  BP_ERR_UNSORTED = 2, /* encoder input not strictly increasing          */
+  BP_ERR_CORRUPT = 3,  /* malformed compressed stream                    */
+  BP_ERR_CAPACITY = 4, /* output buffer too small                        */
+  BP_ERR_CUDA = 5,     /* a CUDA launch or API call failed               */
+  BP_ERR_TIMEOUT = 6,  /* a bounded device wait gave up                  */
+  BP_ERR_SCRATCH = 7   /* scratch buffer too small                       */
+} bp_status;
+
+typedef enum {
+  /* The paper's S4-BP128-D4 byte layout (Section 4.3): meta-blocks of 16
+   * width bytes followed by 16 blocks of 128 integers, each block 4b words in
+   * the 4-lane interleave of Fig. 2 holding D4 deltas (Section 5) carried
+   * from block to block; leftover whole blocks each with their own width
+   * byte; fewer than 128 final integers as varint (Section 4.1).  Our
+   * reading of what the paper leaves open: a 16-byte header
+   * {u32 n, u32 0, u32 tail_bytes, u32 0} and D1 gaps in the varint tail. */
+  BP_LAYOUT_PAPER = 0,
+  /* The GPU layout: same 128-integer blocks, one bit width per block and D4
+   * deltas, but each block restarts D4 from its first value (a per-block
+   * skip header), and a block's deltas are stored column-major -- the delta
+   * of in-block position 4t+s at bit b*(32s+t) -- so that warp lane l
+   * (column l/8, rows 4(l%8)..4(l%8)+3) reads one contiguous 4b-bit field.
+   * Header (64 bytes, u32 little endian): magic 0x344C4742, layout 1, n,
+   * nblocks, nsuper, payload_words, off_first, off_sbo, off_bw, off_payload,
+   * total bytes (u64), zeros; then first[nblocks] u32 (x[128k]),
+   * sbo[nsuper+1] u32 (payload word offset of every 32nd block),
+   * bw[nblocks] u8 (bit widths), payload words; sections 16-byte aligned. */
+  BP_LAYOUT_GPU = 1
+} bp_layout;
+
+/* One list of a batch.  Filled by the caller except unit_base, which
+ * bp_plan_lists() fills. */
+typedef struct bp_list {
+  uint64_t enc_offset; /* byte offset of the stream in the data buffer;
+                          16-byte aligned                                   */
+  uint64_t enc_bytes;  /* size of the stream in bytes                       */
+  uint64_t out_offset; /* element offset of the decoded list in the output  */
+  uint64_t unit_base;  /* first work unit of this list (bp_plan_lists)      */
+  uint32_t n;          /* number of integers, equal to the stream header    */
+  uint32_t layout;     /* bp_layout; all lists of one call share it         */
+  uint64_t reserved;
+} bp_list;
+
+/* Status text for a bp_status code (static string, never NULL). */
+const char *bp_status_string(int status);
+
+/* ---------------------------------------------------------------- host -- */
+
+/* Upper bound of the encoded size of n integers in `layout`. */
+size_t bp_encode_bound(size_t n, int layout);
+
+/* Encode n strictly increasing uint32 (Section 3: sorted distinct docIDs)
+ * into out[0..cap) in `layout`; *out_bytes receives the size.  Errors:
+ * BP_ERR_UNSORTED, BP_ERR_CAPACITY (cap < bp_encode_bound), BP_ERR_ARG.
+ * nthreads <= 1 encodes on the calling thread; more split the blocks over
+ * that many host threads (the output is identical). */
+int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
+              size_t cap, size_t *out_bytes, int nthreads);
+
+/* Parse a stream header on the host: *n_out = number of integers,
+ * *layout_out = its layout.  BP_ERR_CORRUPT if the header is invalid. */
+int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
+                   int *layout_out);
+
+/* Fill lists[i].unit_base for a batch of `count` lists of one layout and
+ * return the total number of work units (GL: groups of 32 blocks; PL: blocks
+ * of 128 integers plus one unit for each list's tail). */
+uint64_t bp_plan_lists(bp_list *lists, uint32_t count);
+
+/* -------------------------------------------------------------- device -- */
+
+/* Scratch needed by bp_decode / bp_decode_sum for a list of n integers
+ * (0 for BP_LAYOUT_GPU; PL needs per-block offsets and scan state). */
+size_t bp_decode_scratch_bytes(size_t n, int layout);
+
+/* Decode one compressed list of n integers (Section 4.3 container;
+ * Algorithm 1 unpacking with the D4 prefix of Section 5).  d_enc: device
+ * stream of enc_bytes bytes, 16-byte aligned; n: its integer count (from
+ * bp_encode or bp_stream_info), which the device checks against the stream
+ * header (mismatch: BP_ERR_CORRUPT); d_out: out_cap >= n uint32 (else
+ * BP_ERR_CAPACITY, returned at once).  A corrupt stream records
+ * BP_ERR_CORRUPT in *d_status and leaves the output undefined.  Scratch:
+ * bp_decode_scratch_bytes(n, layout); the call also enqueues a memset of
+ * part of it. */
+int bp_decode(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n,
+              uint32_t *d_out, size_t out_cap, void *d_scratch,
+              size_t scratch_bytes, uint32_t *d_status, void *stream);
+
+/* As bp_decode, but instead of storing the list adds the exact sum of its
+ * values (mod 2^64) to *d_sum (a device uint64 the caller zeroes). */
+int bp_decode_sum(const uint8_t *d_enc, size_t enc_bytes, int layout,
+                  size_t n, uint64_t *d_sum, void *d_scratch,
+                  size_t scratch_bytes, uint32_t *d_status, void *stream);
+
+/* Scratch needed by bp_decode_batch for these lists (host array). */
+size_t bp_decode_batch_scratch_bytes(const bp_list *lists, uint32_t count);
+
+/* Decode `count` lists of one layout in one pass.  d_data: device buffer the
+ * streams live in; d_lists: device copy of the planned descriptors
+ * (bp_plan_lists); total_units: its return value.  List i is written to
+ * d_out[out_offset .. out_offset + n) (out_cap elements in total).  If
+ * d_sums is not NULL the lists are summed instead of stored: d_sums[i] +=
+ * sum of list i (device uint64, zeroed by the caller) and d_out is unused. */
+int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists,
+                    uint32_t count, uint64_t total_units, int layout,
+                    uint32_t *d_out, uint64_t out_cap, uint64_t *d_sums,
+                    void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,122 @@
+"""PyTorch-facing helpers over the C ABI.  PyTorch only allocates device
+memory and supplies streams; every step of decoding and intersection runs in
+libbp128.so's kernels.  The helpers that return results synchronise the
+stream to read the device status word and raise BPError on a data error."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+from .capi import BP_LIST, BP_LAYOUT_GPU, BP_LAYOUT_PAPER, check  # noqa: F401
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def status_tensor(device="cuda") -> torch.Tensor:
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def check_status(status: torch.Tensor, what: str) -> None:
+    code = int(status.item())
+    if code != capi.BP_OK:
+        raise capi.BPError(code, what)
+
+
+def to_device(enc: np.ndarray, device="cuda") -> torch.Tensor:
+    """Copy an encoded stream (uint8) to the device (torch allocations are
+    256-byte aligned, which meets the 16-byte rule of the ABI)."""
+    t = torch.from_numpy(np.ascontiguousarray(enc, np.uint8))
+    return t.to(device, non_blocking=False)
+
+
+def as_u32(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+def decode(enc_dev: torch.Tensor, layout: int, n: int, stream=None) -> torch.Tensor:
+    if stream is not None:
+        with torch.cuda.stream(stream):
+            return decode(enc_dev, layout, n)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=enc_dev.device)
+    sb = capi.bp_decode_scratch_bytes(n, layout)
+    scratch = torch.empty(max(sb, 1), dtype=torch.uint8, device=enc_dev.device)
+    st = status_tensor(enc_dev.device)
+    check(capi.bp_decode(enc_dev.data_ptr(), enc_dev.numel(), layout, n, out.data_ptr(), n,
+                         scratch.data_ptr(), sb, st.data_ptr(), _stream(stream)), "bp_decode")
+    check_status(st, "bp_decode")
+    return out[:n]
+
+
+def decode_sum(enc_dev: torch.Tensor, layout: int, n: int, stream=None) -> int:
+    if stream is not None:
+        with torch.cuda.stream(stream):
+            return decode_sum(enc_dev, layout, n)
+    acc = torch.zeros(1, dtype=torch.int64, device=enc_dev.device)
+    sb = capi.bp_decode_scratch_bytes(n, layout)
+    scratch = torch.empty(max(sb, 1), dtype=torch.uint8, device=enc_dev.device)
+    st = status_tensor(enc_dev.device)
+    check(capi.bp_decode_sum(enc_dev.data_ptr(), enc_dev.numel(), layout, n, acc.data_ptr(),
+                             scratch.data_ptr(), sb, st.data_ptr(), _stream(stream)),
+          "bp_decode_sum")
+    check_status(st, "bp_decode_sum")
+    return int(acc.item()) & ((1 << 64) - 1)
+
+
+class ListBatch:
+    """Several encoded lists of one layout packed into one device buffer
+    (each stream 16-byte aligned) with planned descriptors."""
+
+    def __init__(self, encs: list[np.ndarray], counts: list[int], layout: int, device="cuda"):
+        self.layout = layout
+        self.count = len(encs)
+        offs, pos = [], 0
+        for e in encs:
+            offs.append(pos)
+            pos += (e.size + 15) // 16 * 16
+        host = np.zeros(max(pos, 16), np.uint8)
+        for o, e in zip(offs, encs):
+            host[o:o + e.size] = e
+        lists = np.zeros(self.count, BP_LIST)
+        out_off = 0
+        for i, (o, e, n) in enumerate(zip(offs, encs, counts)):
+            lists[i] = (o, e.size, out_off, 0, n, layout, 0)
+            out_off += n
+        self.total_units = capi.bp_plan_lists(lists)
+        self.lists = lists
+        self.total_n = out_off
+        self.host_data = host
+        self.data = to_device(host, device)
+        self.d_lists = torch.from_numpy(lists.view(np.uint8).copy()).to(device)
+        self.scratch_bytes = capi.bp_decode_batch_scratch_bytes(lists)
+        self.scratch = torch.empty(max(self.scratch_bytes, 1), dtype=torch.uint8, device=device)
+        self.compressed_bytes = int(sum(e.size for e in encs))
+
+    def decode_into(self, out: torch.Tensor, status: torch.Tensor, stream=None) -> None:
+        check(capi.bp_decode_batch(self.data.data_ptr(), self.d_lists.data_ptr(), self.count,
+                                   self.total_units, self.layout, out.data_ptr(), out.numel(),
+                                   None, self.scratch.data_ptr(), self.scratch_bytes,
+                                   status.data_ptr(), _stream(stream)), "bp_decode_batch")
+
+    def sum_into(self, sums: torch.Tensor, status: torch.Tensor, stream=None) -> None:
+        check(capi.bp_decode_batch(self.data.data_ptr(), self.d_lists.data_ptr(), self.count,
+                                   self.total_units, self.layout, None, 0, sums.data_ptr(),
+                                   self.scratch.data_ptr(), self.scratch_bytes,
+                                   status.data_ptr(), _stream(stream)), "bp_decode_batch")
+
+    def decode(self) -> torch.Tensor:
+        out = torch.empty(max(self.total_n, 1), dtype=torch.int32, device=self.data.device)
+        st = status_tensor(self.data.device)
+        self.decode_into(out, st)
+        check_status(st, "bp_decode_batch")
+        return out[: self.total_n]
+
+    def sums(self) -> np.ndarray:
+        s = torch.zeros(self.count, dtype=torch.int64, device=self.data.device)
+        st = status_tensor(self.data.device)
+        self.sum_into(s, st)
+        check_status(st, "bp_decode_batch")
+        return s.cpu().numpy().view(np.uint64)

@@ -1,0 +1,125 @@
+"""ctypes binding of libbp128.so (include/bp128.h): same names, argument
+marshalling only.  Device pointers are plain ints (e.g. tensor.data_ptr()),
+streams are cudaStream_t handles as ints (torch.cuda.Stream.cuda_stream).
+
+The library must have been built (paper_1401_6399_gb300.build.build());
+importing this module without it raises at once -- there is no fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+BP_OK, BP_ERR_ARG, BP_ERR_UNSORTED, BP_ERR_CORRUPT = 0, 1, 2, 3
+BP_ERR_CAPACITY, BP_ERR_CUDA, BP_ERR_TIMEOUT, BP_ERR_SCRATCH = 4, 5, 6, 7
+BP_LAYOUT_PAPER, BP_LAYOUT_GPU = 0, 1
+
+# struct bp_list (48 bytes)
+BP_LIST = np.dtype([("enc_offset", "<u8"), ("enc_bytes", "<u8"), ("out_offset", "<u8"),
+                    ("unit_base", "<u8"), ("n", "<u4"), ("layout", "<u4"),
+                    ("reserved", "<u8")])
+assert BP_LIST.itemsize == 48
+
+if not os.path.exists(LIB):
+    raise ImportError(f"{LIB} is missing: build it with paper_1401_6399_gb300.build.build()")
+
+lib = C.CDLL(LIB)
+
+_vp, _sz, _u64, _u32, _int = C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint32, C.c_int
+
+
+def _decl(name, restype, *argtypes):
+    f = getattr(lib, name)
+    f.restype = restype
+    f.argtypes = list(argtypes)
+    return f
+
+
+_decl("bp_status_string", C.c_char_p, _int)
+_decl("bp_encode_bound", _sz, _sz, _int)
+_decl("bp_encode", _int, _vp, _sz, _int, _vp, _sz, C.POINTER(_sz), _int)
+_decl("bp_stream_info", _int, _vp, _sz, C.POINTER(_u32), C.POINTER(_int))
+_decl("bp_plan_lists", _u64, _vp, _u32)
+_decl("bp_decode_scratch_bytes", _sz, _sz, _int)
+_decl("bp_decode", _int, _vp, _sz, _int, _sz, _vp, _sz, _vp, _sz, _vp, _vp)
+_decl("bp_decode_sum", _int, _vp, _sz, _int, _sz, _vp, _vp, _sz, _vp, _vp)
+_decl("bp_decode_batch_scratch_bytes", _sz, _vp, _u32)
+_decl("bp_decode_batch", _int, _vp, _vp, _u32, _u64, _int, _vp, _u64, _vp, _vp, _sz, _vp, _vp)
+
+
+class BPError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = lib.bp_status_string(code).decode()
+        super().__init__(f"{what}: {msg} ({code})")
+        self.code = code
+
+
+def check(code: int, what: str) -> None:
+    if code != BP_OK:
+        raise BPError(code, what)
+
+
+def bp_status_string(code: int) -> str:
+    return lib.bp_status_string(code).decode()
+
+
+# ---- host -----------------------------------------------------------------------
+
+def bp_encode_bound(n: int, layout: int) -> int:
+    return int(lib.bp_encode_bound(n, layout))
+
+
+def bp_encode(x, layout: int, nthreads: int = 1) -> np.ndarray:
+    """Encode a sorted distinct uint32 array; returns the stream as uint8."""
+    x = np.ascontiguousarray(x, np.uint32)
+    cap = bp_encode_bound(x.size, layout)
+    out = np.empty(max(cap, 16), np.uint8)
+    nbytes = _sz(0)
+    check(lib.bp_encode(x.ctypes.data if x.size else None, x.size, layout, out.ctypes.data,
+                        cap, C.byref(nbytes), nthreads), "bp_encode")
+    return out[: nbytes.value]
+
+
+def bp_stream_info(enc) -> tuple[int, int]:
+    enc = np.ascontiguousarray(np.frombuffer(bytes(enc), np.uint8) if isinstance(enc, (bytes, bytearray)) else enc, np.uint8)
+    n, layout = _u32(0), _int(0)
+    check(lib.bp_stream_info(enc.ctypes.data, enc.size, C.byref(n), C.byref(layout)),
+          "bp_stream_info")
+    return int(n.value), int(layout.value)
+
+
+def bp_plan_lists(lists: np.ndarray) -> int:
+    assert lists.dtype == BP_LIST and lists.flags.c_contiguous
+    return int(lib.bp_plan_lists(lists.ctypes.data, lists.size))
+
+
+# ---- device (raw pointers) ---------------------------------------------------------
+
+def bp_decode_scratch_bytes(n: int, layout: int) -> int:
+    return int(lib.bp_decode_scratch_bytes(n, layout))
+
+
+def bp_decode(d_enc, enc_bytes, layout, n, d_out, out_cap, d_scratch, scratch_bytes,
+              d_status, stream) -> int:
+    return lib.bp_decode(d_enc, enc_bytes, layout, n, d_out, out_cap, d_scratch,
+                         scratch_bytes, d_status, stream)
+
+
+def bp_decode_sum(d_enc, enc_bytes, layout, n, d_sum, d_scratch, scratch_bytes, d_status,
+                  stream) -> int:
+    return lib.bp_decode_sum(d_enc, enc_bytes, layout, n, d_sum, d_scratch, scratch_bytes,
+                             d_status, stream)
+
+
+def bp_decode_batch_scratch_bytes(lists: np.ndarray) -> int:
+    assert lists.dtype == BP_LIST and lists.flags.c_contiguous
+    return int(lib.bp_decode_batch_scratch_bytes(lists.ctypes.data, lists.size))
+
+
+def bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap, d_sums,
+                    d_scratch, scratch_bytes, d_status, stream) -> int:
+    return lib.bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap,
+                               d_sums, d_scratch, scratch_bytes, d_status, stream)

@@ -1,0 +1,99 @@
+// capi.cu -- extern "C" entry points of the device-side decode calls.
+#include <mutex>
+
+#include "decode.h"
+
+namespace bp {
+
+int device_sm_count() {
+  // cached per device: the SM count never changes for a device
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  std::lock_guard<std::mutex> g(mu);
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+}  // namespace bp
+
+using bp::ListSrc;
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int decode_common(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, uint32_t *d_out,
+                  size_t out_cap, uint64_t *d_sum, void *d_scratch, size_t scratch_bytes,
+                  uint32_t *d_status, void *stream) {
+  if (!d_enc || !d_status || !aligned16(d_enc)) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (n > bp_fmt::kMaxList) return BP_ERR_ARG;
+  if (!d_sum) {
+    if (!d_out && n) return BP_ERR_ARG;
+    if (out_cap < n) return BP_ERR_CAPACITY;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const ListSrc src = bp::single_list(enc_bytes, n, layout);
+  const uint64_t units = bp_fmt::units_of(n, layout);
+  if (layout == BP_LAYOUT_GPU)
+    return bp::launch_gl_decode(d_enc, src, units, d_out, n, d_sum, d_status, s);
+  return bp::launch_pl_decode(d_enc, src, units, d_out, n, d_sum, d_scratch, scratch_bytes,
+                              d_status, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bp_decode_scratch_bytes(size_t n, int layout) {
+  if (layout != BP_LAYOUT_PAPER) return 0;
+  return bp::pl_scratch_bytes(bp_fmt::units_of(n, layout), 1);
+}
+
+int bp_decode(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, uint32_t *d_out,
+              size_t out_cap, void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+              void *stream) {
+  return decode_common(d_enc, enc_bytes, layout, n, d_out, out_cap, nullptr, d_scratch,
+                       scratch_bytes, d_status, stream);
+}
+
+int bp_decode_sum(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, uint64_t *d_sum,
+                  void *d_scratch, size_t scratch_bytes, uint32_t *d_status, void *stream) {
+  if (!d_sum) return BP_ERR_ARG;
+  return decode_common(d_enc, enc_bytes, layout, n, nullptr, 0, d_sum, d_scratch, scratch_bytes,
+                       d_status, stream);
+}
+
+size_t bp_decode_batch_scratch_bytes(const bp_list *lists, uint32_t count) {
+  if (!lists || count == 0 || lists[0].layout != BP_LAYOUT_PAPER) return 0;
+  uint64_t units = 0;
+  for (uint32_t i = 0; i < count; i++) units += bp_fmt::units_of(lists[i].n, BP_LAYOUT_PAPER);
+  return bp::pl_scratch_bytes(units, count);
+}
+
+int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists, uint32_t count,
+                    uint64_t total_units, int layout, uint32_t *d_out, uint64_t out_cap,
+                    uint64_t *d_sums, void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+                    void *stream) {
+  if (!d_data || !d_lists || !d_status || count == 0 || !aligned16(d_data)) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (!d_sums && !d_out) return BP_ERR_ARG;
+  ListSrc src;
+  src.lists = d_lists;
+  src.count = count;
+  src.one = bp_list{};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (layout == BP_LAYOUT_GPU)
+    return bp::launch_gl_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_status, s);
+  return bp::launch_pl_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_scratch,
+                              scratch_bytes, d_status, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// decode.h -- internal launchers of the decode kernels (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/bp128.h"
+#include "format.h"
+
+namespace bp {
+
+// The lists of one call: a device array (batch calls) or a single descriptor
+// passed by value (single-list calls, which have no device array).
+struct ListSrc {
+  const bp_list *lists;  // device array, or nullptr to use `one`
+  uint32_t count;
+  bp_list one;
+#ifdef __CUDACC__
+  __device__ __forceinline__ bp_list get(uint32_t i) const { return lists ? lists[i] : one; }
+  __device__ __forceinline__ uint64_t unit_base(uint32_t i) const {
+    return lists ? lists[i].unit_base : one.unit_base;
+  }
+  // list owning global unit u: largest i with unit_base(i) <= u
+  __device__ __forceinline__ uint32_t find(uint64_t u) const {
+    uint32_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (unit_base(mid) <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
+#endif
+};
+
+inline ListSrc single_list(size_t enc_bytes, size_t n, int layout) {
+  ListSrc s;
+  s.lists = nullptr;
+  s.count = 1;
+  s.one = bp_list{0, enc_bytes, 0, 0, (uint32_t)n, (uint32_t)layout, 0};
+  return s;
+}
+
+int device_sm_count();
+
+// GL layout.  sums == nullptr: store into out; else sums[i] += sum of list i.
+int launch_gl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_units,
+                     uint32_t *out, uint64_t out_cap, uint64_t *sums, uint32_t *status,
+                     cudaStream_t s);
+
+// Paper layout (needs scratch: pl_scratch_bytes).
+size_t pl_scratch_bytes(uint64_t total_units, uint32_t count);
+int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_units,
+                     uint32_t *out, uint64_t out_cap, uint64_t *sums, void *scratch,
+                     size_t scratch_bytes, uint32_t *status, cudaStream_t s);
+
+}  // namespace bp

@@ -1,0 +1,129 @@
+// decode_gl.cu -- decoding of GPU-layout (GL) streams (bp_decode,
+// bp_decode_sum and bp_decode_batch with BP_LAYOUT_GPU).
+//
+// Work unit: a superblock of 32 blocks (4096 integers) per warp; a persistent
+// grid strides over the units of all lists.  Every block decodes on its own
+// from its skip header, so no carry crosses blocks (Section 4.3 container,
+// Algorithm 1 with the D4 prefix of Section 5 restarted per block).
+#include "decode.h"
+#include "gl_block.cuh"
+
+namespace bp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMinBlocks = 5;  // 40 resident warps per SM
+
+template <bool SUM>
+__device__ __forceinline__ void gl_decode_unit(const GlView &v, uint32_t q, int lane,
+                                               uint32_t *__restrict__ out, uint64_t &acc,
+                                               uint32_t *status) {
+  SuperInfo si;
+  if (!gl_super(v, q, lane, si, status)) return;
+  for (uint32_t j = 0; j < si.nblk; j++) {
+    const int b = (int)__shfl_sync(kFull, si.b, j);
+    const uint32_t F = __shfl_sync(kFull, si.F, j);
+    const uint32_t woff = __shfl_sync(kFull, si.woff, j);
+    const uint32_t blk = q * 32u + j;
+    uint32_t x[4];
+    gl_block_values(b, v.payload + woff, F, lane, x);
+    const uint32_t cnt = min(128u, v.n - 128u * blk);
+    if (SUM) {
+#pragma unroll
+      for (int t = 0; t < 4; t++)
+        if ((uint32_t)gl_pos(lane, t) < cnt) acc += x[t];
+    } else {
+      uint32_t *o = out + 128ull * blk;
+      if (cnt == 128u) {
+#pragma unroll
+        for (int t = 0; t < 4; t++) o[gl_pos(lane, t)] = x[t];
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+          if ((uint32_t)gl_pos(lane, t) < cnt) o[gl_pos(lane, t)] = x[t];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane) {
+#pragma unroll
+  for (int dd = 16; dd > 0; dd >>= 1) acc += __shfl_down_sync(kFull, acc, dd);
+  if (lane == 0 && acc)
+    atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)acc);
+  acc = 0;
+}
+
+// Unit u belongs to the list with the largest unit_base <= u; the warp keeps
+// the current list's parsed header while consecutive units stay in it.
+template <bool SUM>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    gl_decode_kernel(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
+                     uint32_t *__restrict__ out, uint64_t out_cap, uint64_t *sums,
+                     uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kThreads) >> 5;
+  uint32_t cur = 0xFFFFFFFFu;
+  bool ok = false;
+  GlView v;
+  uint64_t base = 0, out_off = 0, acc = 0;
+  for (uint64_t u = warp; u < total_units; u += nwarps) {
+    const uint32_t li = src.find(u);
+    if (li != cur) {
+      if (SUM && cur != 0xFFFFFFFFu) flush_sum(acc, sums + cur, lane);
+      cur = li;
+      const bp_list L = src.get(li);
+      base = L.unit_base;
+      out_off = L.out_offset;
+      ok = gl_view(data + L.enc_offset, L.enc_bytes, v) && v.n == L.n;
+      if (!ok) {
+        if (lane == 0) set_status(status, BP_ERR_CORRUPT);
+      } else if (!SUM && L.out_offset + L.n > out_cap) {
+        ok = false;
+        if (lane == 0) set_status(status, BP_ERR_CAPACITY);
+      }
+    }
+    if (!ok) continue;
+    const uint64_t q = u - base;
+    if (q >= v.nsuper) continue;
+    gl_decode_unit<SUM>(v, (uint32_t)q, lane, out + out_off, acc, status);
+  }
+  if (SUM && cur != 0xFFFFFFFFu) flush_sum(acc, sums + cur, lane);
+}
+
+template <class K>
+int persistent_grid(K kernel, uint64_t units, int &per_sm_cache) {
+  if (per_sm_cache < 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    per_sm_cache = nb;
+  }
+  const uint64_t want = (units + (kThreads / 32) - 1) / (kThreads / 32);
+  const uint64_t cap = (uint64_t)per_sm_cache * device_sm_count();
+  return (int)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
+int launch_gl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_units,
+                     uint32_t *out, uint64_t out_cap, uint64_t *sums, uint32_t *status,
+                     cudaStream_t s) {
+  if (total_units == 0) return BP_OK;
+  static int occ_sum = -1, occ_store = -1;
+  if (sums) {
+    const int grid = persistent_grid(gl_decode_kernel<true>, total_units, occ_sum);
+    gl_decode_kernel<true><<<grid, kThreads, 0, s>>>(data, src, total_units, out, out_cap, sums,
+                                                     status);
+  } else {
+    const int grid = persistent_grid(gl_decode_kernel<false>, total_units, occ_store);
+    gl_decode_kernel<false><<<grid, kThreads, 0, s>>>(data, src, total_units, out, out_cap, sums,
+                                                      status);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
+}
+
+}  // namespace bp

@@ -1,0 +1,272 @@
+// encode.cpp -- host encoder for the S4-BP128-D4 paper layout and the GPU
+// layout, plus stream-header parsing and batch planning (C ABI in bp128.h).
+//
+// Section 4.3 (container), Section 4.2 / Fig. 2 (4-lane interleave),
+// Section 5 (D4 differential coding), Section 4.1 (varint tail).
+#include <algorithm>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "../../include/bp128.h"
+#include "format.h"
+
+namespace {
+
+inline unsigned width_of(uint32_t v) { return v ? 32u - (unsigned)__builtin_clz(v) : 0u; }
+
+inline void put_le32(uint8_t *p, uint32_t v) { std::memcpy(p, &v, 4); }
+
+// Run f(lo, hi) over [0, count) split into `nthreads` contiguous ranges.
+template <class F>
+void parallel_ranges(size_t count, int nthreads, F f) {
+  if (nthreads <= 1 || count < 4096) {
+    f(size_t(0), count);
+    return;
+  }
+  const size_t nt = std::min<size_t>((size_t)nthreads, 256);
+  std::vector<std::thread> th;
+  const size_t step = (count + nt - 1) / nt;
+  for (size_t t = 0; t < nt; t++) {
+    const size_t lo = t * step, hi = std::min(count, lo + step);
+    if (lo >= hi) break;
+    th.emplace_back([=] { f(lo, hi); });
+  }
+  for (auto &x : th) x.join();
+}
+
+// ---- paper layout ---------------------------------------------------------
+
+// Pack 128 D4 deltas of one block in the 4-lane interleave (Fig. 2):
+// integer n -> lane n%4, slot n/4, lane word k at block word 4k+lane.
+void pack_s4(const uint32_t *d, unsigned b, uint32_t *w) {
+  std::memset(w, 0, 16 * b);
+  if (!b) return;
+  for (unsigned lane = 0; lane < 4; lane++) {
+    unsigned bit = 0;
+    for (unsigned slot = 0; slot < 32; slot++, bit += b) {
+      const uint32_t v = d[4 * slot + lane];
+      const unsigned k = bit >> 5, o = bit & 31;
+      w[4 * k + lane] |= v << o;
+      if (o + b > 32) w[4 * (k + 1) + lane] |= v >> (32 - o);
+    }
+  }
+}
+
+int encode_paper(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
+                 size_t *out_bytes, int nthreads) {
+  const size_t nb = n / 128, np = nb * 128, meta = nb / 16;
+  std::vector<uint8_t> widths(nb);
+  parallel_ranges(nb, nthreads, [&](size_t lo, size_t hi) {
+    for (size_t k = lo; k < hi; k++) {
+      uint32_t m = 0;
+      for (unsigned i = 0; i < 128; i++) {
+        const size_t g = 128 * k + i;
+        m |= x[g] - (g >= 4 ? x[g - 4] : 0u);
+      }
+      widths[k] = (uint8_t)width_of(m);  // OR has the same width as the max
+    }
+  });
+  // byte offset of every block
+  std::vector<size_t> boff(nb + 1);
+  size_t pos = bp_fmt::kPaperHeader;
+  for (size_t k = 0; k < nb; k++) {
+    if (k < 16 * meta) {
+      if (k % 16 == 0) pos += 16;
+    } else {
+      pos += 1;
+    }
+    boff[k] = pos;
+    pos += 16 * (size_t)widths[k];
+  }
+  const size_t body_end = pos;
+  // tail: varint of D1 gaps
+  uint8_t tailbuf[128 * 5];
+  size_t tail = 0;
+  uint32_t prev = np ? x[np - 1] : 0u;
+  for (size_t i = np; i < n; i++) {
+    uint32_t g = x[i] - prev;
+    prev = x[i];
+    while (g >= 128u) {
+      tailbuf[tail++] = (uint8_t)(g & 127u);
+      g >>= 7;
+    }
+    tailbuf[tail++] = (uint8_t)(g | 128u);
+  }
+  if (body_end + tail > cap) return BP_ERR_CAPACITY;
+
+  put_le32(out + 0, (uint32_t)n);
+  put_le32(out + 4, 0u);
+  put_le32(out + 8, (uint32_t)tail);
+  put_le32(out + 12, 0u);
+  for (size_t m = 0; m < meta; m++) std::memcpy(out + boff[16 * m] - 16, &widths[16 * m], 16);
+  for (size_t k = 16 * meta; k < nb; k++) out[boff[k] - 1] = widths[k];
+  parallel_ranges(nb, nthreads, [&](size_t lo, size_t hi) {
+    uint32_t d[128], w[128];
+    for (size_t k = lo; k < hi; k++) {
+      for (unsigned i = 0; i < 128; i++) {
+        const size_t g = 128 * k + i;
+        d[i] = x[g] - (g >= 4 ? x[g - 4] : 0u);
+      }
+      pack_s4(d, widths[k], w);
+      std::memcpy(out + boff[k], w, 16 * (size_t)widths[k]);
+    }
+  });
+  std::memcpy(out + body_end, tailbuf, tail);
+  *out_bytes = body_end + tail;
+  return BP_OK;
+}
+
+// ---- GPU layout -------------------------------------------------------------
+
+// Column-major packing: delta of position 4t+s at bit b*(32s+t).
+void pack_gl(const uint32_t *d, unsigned b, uint32_t *w) {
+  std::memset(w, 0, 16 * b);
+  if (!b) return;
+  unsigned bit = 0;
+  for (unsigned s = 0; s < 4; s++)
+    for (unsigned t = 0; t < 32; t++, bit += b) {
+      const uint32_t v = d[4 * t + s];
+      const unsigned k = bit >> 5, o = bit & 31;
+      w[k] |= v << o;
+      if (o + b > 32) w[k + 1] |= v >> (32 - o);
+    }
+}
+
+// Deltas of block k with the seed (F,F,F,F); a short last block is padded
+// so that every missing delta is zero.
+void gl_deltas(const uint32_t *x, size_t n, size_t k, uint32_t *d) {
+  const size_t base = 128 * k;
+  const unsigned cnt = (unsigned)std::min<size_t>(128, n - base);
+  const uint32_t F = x[base];
+  uint32_t xx[128];
+  for (unsigned i = 0; i < 128; i++)
+    xx[i] = i < cnt ? x[base + i] : (i >= 4 ? xx[i - 4] : F);
+  for (unsigned i = 0; i < 128; i++) d[i] = xx[i] - (i >= 4 ? xx[i - 4] : F);
+}
+
+int encode_gpu(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
+               size_t *out_bytes, int nthreads) {
+  const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(n);
+  std::vector<uint8_t> widths(g.nblocks);
+  parallel_ranges(g.nblocks, nthreads, [&](size_t lo, size_t hi) {
+    uint32_t d[128];
+    for (size_t k = lo; k < hi; k++) {
+      gl_deltas(x, n, k, d);
+      uint32_t m = 0;
+      for (unsigned i = 0; i < 128; i++) m |= d[i];
+      widths[k] = (uint8_t)width_of(m);
+    }
+  });
+  std::vector<uint64_t> woff(g.nblocks + 1);
+  uint64_t w = 0;
+  for (size_t k = 0; k < g.nblocks; k++) {
+    woff[k] = w;
+    w += 4 * (uint64_t)widths[k];
+  }
+  woff[g.nblocks] = w;
+  if (w > 0xFFFFFFFFull) return BP_ERR_ARG;
+  const size_t total = g.off_payload + 4 * (size_t)w;
+  if (total > cap) return BP_ERR_CAPACITY;
+
+  std::memset(out, 0, g.off_payload);
+  uint32_t hdr[16] = {bp_fmt::kGlMagic, 1u, (uint32_t)n, (uint32_t)g.nblocks,
+                      (uint32_t)g.nsuper, (uint32_t)w, (uint32_t)g.off_first,
+                      (uint32_t)g.off_sbo, (uint32_t)g.off_bw,
+                      (uint32_t)g.off_payload, (uint32_t)(total & 0xFFFFFFFFu),
+                      (uint32_t)((uint64_t)total >> 32), 0, 0, 0, 0};
+  std::memcpy(out, hdr, 64);
+  for (size_t q = 0; q <= g.nsuper; q++)
+    put_le32(out + g.off_sbo + 4 * q, (uint32_t)woff[std::min(32 * q, g.nblocks)]);
+  std::memcpy(out + g.off_bw, widths.data(), g.nblocks);
+  parallel_ranges(g.nblocks, nthreads, [&](size_t lo, size_t hi) {
+    uint32_t d[128], wb[128];
+    for (size_t k = lo; k < hi; k++) {
+      put_le32(out + g.off_first + 4 * k, x[128 * k]);
+      gl_deltas(x, n, k, d);
+      pack_gl(d, widths[k], wb);
+      std::memcpy(out + g.off_payload + 4 * woff[k], wb, 16 * (size_t)widths[k]);
+    }
+  });
+  *out_bytes = total;
+  return BP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bp_encode_bound(size_t n, int layout) {
+  if (layout == BP_LAYOUT_PAPER) {
+    const size_t nb = n / 128;
+    return bp_fmt::kPaperHeader + (nb / 16) * 16 + nb % 16 + nb * 512 + (n % 128) * 5;
+  }
+  if (layout == BP_LAYOUT_GPU) {
+    const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(n);
+    return g.off_payload + 512 * g.nblocks;
+  }
+  return 0;
+}
+
+int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
+              size_t cap, size_t *out_bytes, int nthreads) {
+  if (!out || !out_bytes || (n && !in)) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (n > bp_fmt::kMaxList) return BP_ERR_ARG;
+  for (size_t i = 1; i < n; i++)
+    if (in[i] <= in[i - 1]) return BP_ERR_UNSORTED;
+  if (cap < bp_encode_bound(n, layout)) return BP_ERR_CAPACITY;
+  return layout == BP_LAYOUT_PAPER ? encode_paper(in, n, out, cap, out_bytes, nthreads)
+                                   : encode_gpu(in, n, out, cap, out_bytes, nthreads);
+}
+
+int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
+                   int *layout_out) {
+  if (!enc || !n_out || !layout_out) return BP_ERR_ARG;
+  uint32_t h[16];
+  if (enc_bytes < 16) return BP_ERR_CORRUPT;
+  std::memcpy(h, enc, 16);
+  if (h[1] == 0u && h[3] == 0u) {
+    *n_out = h[0];
+    *layout_out = BP_LAYOUT_PAPER;
+    return BP_OK;
+  }
+  if (enc_bytes < 64) return BP_ERR_CORRUPT;
+  std::memcpy(h, enc, 64);
+  if (h[0] == bp_fmt::kGlMagic && h[1] == 1u) {
+    const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(h[2]);
+    const uint64_t total = (uint64_t)h[10] | ((uint64_t)h[11] << 32);
+    if (h[3] != g.nblocks || h[4] != g.nsuper || h[9] != g.off_payload ||
+        total != g.off_payload + 4ull * h[5] || total > enc_bytes)
+      return BP_ERR_CORRUPT;
+    *n_out = h[2];
+    *layout_out = BP_LAYOUT_GPU;
+    return BP_OK;
+  }
+  return BP_ERR_CORRUPT;
+}
+
+uint64_t bp_plan_lists(bp_list *lists, uint32_t count) {
+  uint64_t u = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    lists[i].unit_base = u;
+    u += bp_fmt::units_of(lists[i].n, (int)lists[i].layout);
+  }
+  return u;
+}
+
+const char *bp_status_string(int status) {
+  switch (status) {
+    case BP_OK: return "ok";
+    case BP_ERR_ARG: return "invalid argument";
+    case BP_ERR_UNSORTED: return "input not strictly increasing";
+    case BP_ERR_CORRUPT: return "corrupt compressed stream";
+    case BP_ERR_CAPACITY: return "output buffer too small";
+    case BP_ERR_CUDA: return "CUDA error";
+    case BP_ERR_TIMEOUT: return "device wait timed out";
+    case BP_ERR_SCRATCH: return "scratch buffer too small";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// gl_block.cuh -- warp-level decoder of one 128-integer block of the GPU
+// layout (GL).
+//
+// Mapping: warp lane l = 8s + c owns column s (positions = s mod 4) and rows
+// 4c..4c+3 of the block, i.e. block positions 16c + 4j + s, j = 0..3.  In GL
+// those four deltas are the contiguous bits [4bl, 4bl + 4b) of the block's
+// LSB-first bit string, so each lane reads at most five consecutive words.
+//
+// D4 (Section 5): x_i = delta_i + x_{i-4}, i.e. a running sum down each
+// column.  A lane sums its own four rows sequentially (Algorithm 1 applies
+// P(t,v) = t+v one 4-vector at a time; here one column at a time), then the
+// eight lanes of a column combine their totals with a 3-step shuffle scan,
+// and the block's first value F (the GL skip header) is the seed of every
+// column.  The bit extraction is specialised per width b at compile time,
+// as the paper generates one routine per b (Section 4.2).
+#pragma once
+#include "common.cuh"
+
+namespace bp {
+
+// The four deltas of `lane` from a block of width B at w (4B words).
+template <int B>
+__device__ __forceinline__ void gl_lane_deltas(const uint32_t *__restrict__ w, int lane,
+                                               uint32_t d[4]) {
+  if constexpr (B == 0) {
+    d[0] = d[1] = d[2] = d[3] = 0u;
+  } else {
+    constexpr int G = gcd_c(4 * B, 32);
+    constexpr int OMAX = 32 - G;                // largest in-word start offset
+    constexpr int NW = (OMAX + 4 * B + 31) / 32;  // words a lane may touch
+    constexpr int UW = (4 * B + 31) / 32;         // words after alignment
+    const uint32_t p = 4u * B * (uint32_t)lane;
+    const uint32_t w0 = p >> 5, o = p & 31u;
+    uint32_t a[NW + 1];
+#pragma unroll
+    for (int k = 0; k < NW; k++) a[k] = (w0 + k < 4u * B) ? __ldg(w + w0 + k) : 0u;
+    a[NW] = 0u;
+    uint32_t u[UW + 1];
+#pragma unroll
+    for (int k = 0; k < UW; k++) u[k] = (OMAX == 0) ? a[k] : __funnelshift_r(a[k], a[k + 1], o);
+    u[UW] = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int q = B * j, k = q >> 5, r = q & 31;
+      uint32_t v = (r + B <= 32) ? (u[k] >> r) : __funnelshift_r(u[k], u[k + 1], r);
+      d[j] = (B == 32) ? v : (v & ((1u << (B & 31)) - 1u));
+    }
+  }
+}
+
+// Decoded values of `lane`: x[j] is block position 16c + 4j + s.
+template <int B>
+__device__ __forceinline__ void gl_lane_values(const uint32_t *__restrict__ w, uint32_t F,
+                                               int lane, uint32_t x[4]) {
+  uint32_t d[4];
+  gl_lane_deltas<B>(w, lane, d);
+  x[0] = d[0];
+  x[1] = x[0] + d[1];
+  x[2] = x[1] + d[2];
+  x[3] = x[2] + d[3];
+  const int c = lane & 7;
+  uint32_t incl = x[3];
+#pragma unroll
+  for (int dd = 1; dd < 8; dd <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, dd, 8);
+    if (c >= dd) incl += t;
+  }
+  const uint32_t base = F + (incl - x[3]);
+#pragma unroll
+  for (int j = 0; j < 4; j++) x[j] += base;
+}
+
+// Runtime-width dispatch (b is warp-uniform, so the switch never diverges).
+__device__ __forceinline__ void gl_block_values(int b, const uint32_t *__restrict__ w,
+                                                uint32_t F, int lane, uint32_t x[4]) {
+  switch (b) {
+#define BP_CASE(B) \
+  case B:          \
+    gl_lane_values<B>(w, F, lane, x); \
+    break;
+    BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
+    BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
+    BP_CASE(14) BP_CASE(15) BP_CASE(16) BP_CASE(17) BP_CASE(18) BP_CASE(19) BP_CASE(20)
+    BP_CASE(21) BP_CASE(22) BP_CASE(23) BP_CASE(24) BP_CASE(25) BP_CASE(26) BP_CASE(27)
+    BP_CASE(28) BP_CASE(29) BP_CASE(30) BP_CASE(31) BP_CASE(32)
+#undef BP_CASE
+    default:
+      x[0] = x[1] = x[2] = x[3] = 0u;
+  }
+}
+
+// In-block position of x[j] for `lane`.
+__device__ __forceinline__ int gl_pos(int lane, int j) { return 16 * (lane & 7) + 4 * j + (lane >> 3); }
+
+// Superblock q of a GL list as seen by one warp: every lane holds the width,
+// first value and payload word offset of block 32q + lane.  Returns false
+// (and records BP_ERR_CORRUPT) if the widths or offsets are inconsistent.
+struct SuperInfo {
+  uint32_t nblk;  // blocks in this superblock (1..32)
+  uint32_t b, F, woff;  // per lane
+};
+
+__device__ __forceinline__ bool gl_super(const GlView &v, uint32_t q, int lane, SuperInfo &si,
+                                         uint32_t *status) {
+  const uint32_t k0 = q * 32u;
+  si.nblk = min(32u, v.nblocks - k0);
+  uint32_t b = 0, F = 0;
+  if ((uint32_t)lane < si.nblk) {
+    b = v.bw[k0 + lane];
+    F = __ldg(v.first + k0 + lane);
+  }
+  uint32_t incl = 4u * b;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, dd);
+    if (lane >= dd) incl += t;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t base = __ldg(v.sbo + q), end = __ldg(v.sbo + q + 1);
+  const bool bad = __any_sync(kFull, b > 32u) || end < base || end - base != total || end > v.pw;
+  if (bad) {
+    if (lane == 0) set_status(status, BP_ERR_CORRUPT);
+    return false;
+  }
+  si.b = b;
+  si.F = F;
+  si.woff = base + incl - 4u * b;
+  return true;
+}
+
+}  // namespace bp

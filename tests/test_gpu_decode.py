@@ -1,0 +1,189 @@
+"""GPU parity of decoding (bp_decode, bp_decode_sum, bp_decode_batch) against
+the scalar oracle, bit-exact, for both layouts: edge lengths, ragged tails,
+many tiles, mixed widths, full-size lists, corrupt streams."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1401_6399_gb300.build import build  # noqa: E402
+
+build()
+from paper_1401_6399_gb300 import api, capi  # noqa: E402
+
+LAYOUTS = [capi.BP_LAYOUT_PAPER, capi.BP_LAYOUT_GPU]
+
+
+def oracle_decode(orc, x, layout):
+    return orc.pl_decode(orc.pl_encode(x)) if layout == 0 else orc.gl_decode(orc.gl_encode(x))
+
+
+def gpu_decode(x, layout):
+    enc = capi.bp_encode(x, layout, nthreads=8)
+    return api.as_u32(api.decode(api.to_device(enc), layout, x.size))
+
+
+EDGE = [0, 1, 2, 4, 5, 127, 128, 129, 255, 2047, 2048, 2049, 4095, 4096, 4097,
+        3 * 4096 + 129, 16 * 2048 + 15 * 128 + 127, 65536, 65549]
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("n", EDGE)
+def test_decode_edge_lengths(orc, layout, n):
+    rng = np.random.default_rng(n * 3 + layout)
+    for U in (n + 1, 16 * n + 16, 1 << 32):
+        x = np.sort(rng.choice(U, n, replace=False)).astype(np.uint32)
+        got = gpu_decode(x, layout)
+        ref = oracle_decode(orc, x, layout)
+        assert np.array_equal(ref, x)
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_tiny_config(orc, layout):
+    """A = 65,536 and B = 4,096 distinct values of [0, 2^20)."""
+    for n, seed in ((65536, 0x1001), (4096, 0x1002)):
+        x = W.uniform(n, 0, 1 << 20, seed)
+        assert np.array_equal(gpu_decode(x, layout), oracle_decode(orc, x, layout))
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_clustered_many_tiles(orc, layout):
+    """Clustered values mix widths 3..25 inside one list; 2^20+77 integers
+    span thousands of tiles and end in a ragged tail."""
+    x = W.clustered((1 << 20) + 77, 0, 1 << 29, 0x2100)
+    enc = capi.bp_encode(x, layout, nthreads=8)
+    got = api.as_u32(api.decode(api.to_device(enc), layout, x.size))
+    ref = orc.pl_decode(enc.tobytes()) if layout == 0 else orc.gl_decode(enc.tobytes())
+    assert np.array_equal(got, ref)
+    assert np.array_equal(got, x)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_all_widths(orc, layout):
+    """One block of every width 0..32: D4 deltas drawn below 2^w per block
+    (the codec is exact modulo 2^32 for any sequence), streams built bit by
+    bit from the format definition, decoded on the GPU and by the oracle."""
+    import brute
+    rng = np.random.default_rng(7)
+    widths = list(range(33)) + [7, 0, 32]
+    d = []
+    for w in widths:
+        blk = rng.integers(0, 1 << max(w - 1, 0), 128, dtype=np.uint64) if w else \
+            np.zeros(128, np.uint64)
+        if w:
+            blk[rng.integers(1, 128)] = (1 << w) - 1
+        d.append(blk)
+    if layout == 0:  # D4 carried across blocks from (0,0,0,0)
+        d = np.concatenate(d)
+        x = np.zeros(d.size + 37, np.uint64)
+        for i in range(d.size):
+            x[i] = (d[i] + (x[i - 4] if i >= 4 else 0)) % (1 << 32)
+        x[d.size:] = (x[d.size - 1] + np.arange(1, 38)) % (1 << 32)
+    else:  # D4 restarted at every block from its first value F
+        parts = []
+        for blk in d:
+            blk[0] = 0
+            F = int(rng.integers(0, 1 << 32))
+            xb = np.zeros(128, np.uint64)
+            for i in range(128):
+                xb[i] = (int(blk[i]) + (int(xb[i - 4]) if i >= 4 else F)) % (1 << 32)
+            parts.append(xb)
+        x = np.concatenate(parts + [np.arange(5, dtype=np.uint64)])
+    x = x.astype(np.uint32)
+    stream = brute.pl_stream(x) if layout == 0 else brute.gl_stream(x)
+    enc = np.frombuffer(stream, np.uint8)
+    got = api.as_u32(api.decode(api.to_device(enc), layout, x.size))
+    ref = orc.pl_decode(stream) if layout == 0 else orc.gl_decode(stream)
+    assert np.array_equal(ref, x)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_sum(orc, layout):
+    for n, seed in ((0, 1), (100, 2), (65536 + 99, 3), (1 << 20, 4)):
+        x = W.clustered(n, 0, 1 << 31, seed) if n else np.zeros(0, np.uint32)
+        enc = capi.bp_encode(x, layout)
+        got = api.decode_sum(api.to_device(enc), layout, n)
+        ref = oracle_decode(orc, x, layout)
+        assert got == int(ref.astype(np.uint64).sum()) % (1 << 64)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_batch(orc, layout):
+    rng = np.random.default_rng(99)
+    sizes = [0, 1, 130, 4096, 5000, 2048 * 16 + 3, 777, 128 * 33]
+    xs = [np.sort(rng.choice(1 << 30, n, replace=False)).astype(np.uint32) for n in sizes]
+    encs = [capi.bp_encode(x, layout) for x in xs]
+    batch = api.ListBatch(encs, sizes, layout)
+    got = api.as_u32(batch.decode())
+    ref = np.concatenate([oracle_decode(orc, x, layout) for x in xs])
+    assert np.array_equal(got, ref)
+    sums = batch.sums()
+    assert sums.tolist() == [int(x.astype(np.uint64).sum()) for x in xs]
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_full_size_batch(layout):
+    """Four lists of 2^26 integers in [0, 2^29) (two uniform, two clustered),
+    decoded in one batch launch as the benchmark does; a decoded list must be
+    the encoded list (round trip), and the sums must match."""
+    xs, _ = W.many("uniform", [1 << 26] * 2, 0, 1 << 29, 0x2000)
+    xc, _ = W.many("clustered", [1 << 26] * 2, 0, 1 << 29, 0x2000)
+    lists = [xs[:1 << 26], xs[1 << 26:], xc[:1 << 26], xc[1 << 26:]]
+    encs = [capi.bp_encode(x, layout, nthreads=16) for x in lists]
+    batch = api.ListBatch(encs, [x.size for x in lists], layout)
+    got = batch.decode()
+    want = torch.from_numpy(np.concatenate(lists).view(np.int32)).to(got.device)
+    assert torch.equal(got, want)
+    assert batch.sums().tolist() == [int(x.astype(np.uint64).sum()) for x in lists]
+
+
+def _status_of(enc, layout, n, cap=None):
+    d = api.to_device(enc)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    sb = capi.bp_decode_scratch_bytes(n, layout)
+    scratch = torch.empty(max(sb, 1), dtype=torch.uint8, device="cuda")
+    st = api.status_tensor()
+    rc = capi.bp_decode(d.data_ptr(), d.numel(), layout, n, out.data_ptr(),
+                        cap if cap is not None else n, scratch.data_ptr(), sb, st.data_ptr(),
+                        torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return rc, int(st.item())
+
+
+def test_corrupt_streams_record_status():
+    x = np.arange(3, 3 + 5 * 9000, 5, dtype=np.uint32)
+    pl = capi.bp_encode(x, 0).copy()
+    bad = pl.copy()
+    bad[16] = 33  # a width byte beyond 32
+    assert _status_of(bad, 0, x.size) == (capi.BP_OK, capi.BP_ERR_CORRUPT)
+    assert _status_of(pl[:-5], 0, x.size)[1] == capi.BP_ERR_CORRUPT  # truncated
+    assert _status_of(pl, 0, x.size - 1)[1] == capi.BP_ERR_CORRUPT   # wrong n
+    gl = capi.bp_encode(x, 1).copy()
+    off_bw = int(gl[32:36].view(np.uint32)[0])
+    bad = gl.copy()
+    bad[off_bw + 3] = 40
+    assert _status_of(bad, 1, x.size)[1] == capi.BP_ERR_CORRUPT
+    bad = gl.copy()
+    bad[0] ^= 1  # magic
+    assert _status_of(bad, 1, x.size)[1] == capi.BP_ERR_CORRUPT
+    assert _status_of(gl, 1, x.size)[1] == capi.BP_OK
+    assert _status_of(gl, 1, x.size, cap=x.size - 1)[0] == capi.BP_ERR_CAPACITY
+
+
+def test_decode_is_deterministic_across_streams():
+    x = W.clustered(300_000, 0, 1 << 28, 5)
+    for layout in LAYOUTS:
+        enc = api.to_device(capi.bp_encode(x, layout))
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        a = api.decode(enc, layout, x.size, stream=s1)
+        b = api.decode(enc, layout, x.size, stream=s2)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
