@@ -1,0 +1,453 @@
+#!/usr/bin/env python3
+"""Benchmark of the S4-BP128-D4 decode hot path on GB300.
+
+Workload (one step): decode 32 lists of 2^26 sorted distinct uint32 drawn
+uniformly without replacement from [0, 2^29), S4-BP128-D4 encoded in the GPU
+layout, in one bp_decode_batch launch (8 GiB of decoded output per step).
+Inputs (1.9 GB compressed) and outputs (8 GiB) are far larger than L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank decodes its own 32
+lists (weak scaling, no collective on the data path); the reported value is
+all ranks' integers over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "S4-BP128-D4 decoded Gint/s"
+UNIT = "Gint/s"
+N_PER_LIST = 1 << 26
+UNIVERSE = 1 << 29
+SEED_BASE = 0x2000
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--lists", type=int, default=32)
+    p.add_argument("--log2n", type=int, default=26)
+    p.add_argument("--no-extra", action="store_true", help="skip secondary measurements")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ---- distributed plumbing -----------------------------------------------------------
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, local):
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks --------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = [r for (t, r) in self.samples if t0 <= t <= t1 and len(r) >= 8]
+        if not rows:  # timed region shorter than one sample: take the nearest ones
+            rows = [r for (t, r) in self.samples if t0 - 0.3 <= t <= t1 + 0.3 and len(r) >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][1]), "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[2]) or 0) for r in rows)}
+
+
+# ---- workload --------------------------------------------------------------------------
+
+def make_lists(kind: str, count: int, n: int, U: int, seed_base: int):
+    import workloads as W
+    vals, offs = W.many(kind, [n] * count, 0, U, seed_base)
+    return [vals[int(offs[i]):int(offs[i + 1])] for i in range(count)]
+
+
+def encode_all(lists, layout: int):
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1401_6399_gb300 import capi
+    nt = max(1, min(8, (os.cpu_count() or 8) // 2))
+    with ThreadPoolExecutor(max_workers=min(len(lists), 8)) as ex:
+        return list(ex.map(lambda x: capi.bp_encode(x, layout, nthreads=nt), lists))
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("common.cuh", "gl_block.cuh", "decode_gl.cu", "format.h", "decode.h"):
+        with open(os.path.join(ROOT, "paper_1401_6399_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(sha: str):
+    """DRAM bytes per full launch of the headline decode kernel from the
+    committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", "gl_decode_uniform_32x2p26.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---- the oracle as a CPU baseline --------------------------------------------------------
+
+def oracle_decode_rate(encs, ns, threads: int):
+    """Decode the given GL streams with the scalar oracle on `threads` host
+    threads; returns (Gint/s, seconds, threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import Oracle
+    orc = Oracle()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        outs = list(ex.map(lambda e: orc.gl_decode(e.tobytes()), encs))
+    dt = time.perf_counter() - t0
+    assert [o.size for o in outs] == list(ns)
+    return sum(ns) / dt / 1e9, dt, threads
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle (scalar C) on the host cores; each step
+    decodes a bounded sample of the workload: 16 lists of 2^22 integers of
+    the same distribution (uniform, density 1/8, [0, 2^25))."""
+    if rank != 0:
+        return
+    from oracle import build_oracle
+    from workloads.workloads import build_workloads
+    from paper_1401_6399_gb300.build import build
+    build()
+    build_oracle()
+    build_workloads()
+    from paper_1401_6399_gb300 import capi
+    threads = min(16, os.cpu_count() or 1)
+    n = 1 << 22
+    lists = make_lists("uniform", threads, n, 1 << 25, SEED_BASE)
+    encs = [capi.bp_encode(x, capi.BP_LAYOUT_GPU, nthreads=4) for x in lists]
+    for _ in range(args.warmup):
+        oracle_decode_rate(encs, [n] * threads, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_decode_rate(encs, [n] * threads, threads)
+    dt = time.perf_counter() - t0
+    ints = n * threads * args.steps
+    val = ints / dt / 1e9
+    sample = f"{threads} lists x 2^22 uniform ints of [0,2^25) per step, GL streams, scalar oracle"
+    line = {"metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "decode 32 lists x 2^26 uniform uint32 of [0,2^29), S4-BP128-D4 "
+                                   "GPU layout (bounded CPU sample per step)",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm -------------------------------------------------------------------------------
+
+def time_launches(stream, fn, steps: int, warmup: int):
+    """Run fn() warmup + steps times on `stream`; return ms per step from CUDA
+    events recorded on that stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    dist = dist_init(world, local)
+    sys.path.insert(0, ROOT)
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    barrier(dist)
+    ge.build()
+    from paper_1401_6399_gb300 import api, capi
+
+    n = 1 << args.log2n
+    L = args.lists
+    seed = SEED_BASE + 4096 * rank
+    lists = make_lists("uniform", L, n, UNIVERSE, seed)
+    encs = encode_all(lists, capi.BP_LAYOUT_GPU)
+    batch = api.ListBatch(encs, [n] * L, capi.BP_LAYOUT_GPU)
+    total_n = n * L
+    out = torch.empty(total_n, dtype=torch.int32, device="cuda")
+    status = api.status_tensor()
+    stream = torch.cuda.Stream()
+
+    # correctness gate before timing: the decoded lists are the input lists
+    with torch.cuda.stream(stream):
+        batch.decode_into(out, status, stream)
+    stream.synchronize()
+    assert int(status.item()) == 0, "decode reported an error"
+    want = torch.from_numpy(np.concatenate(lists).view(np.int32)).to("cuda")
+    assert torch.equal(out, want), "decoded output differs from the input lists"
+    del want
+
+    def step():
+        batch.decode_into(out, status, stream)
+
+    gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES") or str(local)).split(",")[0]) \
+        if (os.environ.get("CUDA_VISIBLE_DEVICES") or "").split(",")[0].isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    w1 = time.time()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(dist, ms_local)
+    clk = clocks.summary(w0, w1)
+    assert int(status.item()) == 0
+
+    value = world * total_n / (ms * 1e-3) / 1e9  # Gint/s over all ranks
+    comp_bytes = batch.compressed_bytes
+    alg_bytes = comp_bytes + 4 * total_n  # per launch (one launch per step)
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (ms_local * 1e-3) / 1e9
+    sha = kernel_sha()
+    traffic = profiled_traffic(sha)
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"decode {L} lists x 2^{args.log2n} uniform uint32 of [0,2^29) "
+                               "per GPU, S4-BP128-D4 GPU layout, one bp_decode_batch launch",
+                   "lists_per_gpu": L, "ints_per_list": n,
+                   "compressed_bytes_per_gpu": comp_bytes,
+                   "bits_per_int": round(8 * comp_bytes / total_n, 3),
+                   "l2": "inputs (compressed) and outputs larger than L2; no flush",
+                   "parallelism": f"weak x{world}"},
+        "gpu_launches": args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "gl_decode_kernel<false>", "algorithmic_bytes_per_launch": alg_bytes,
+                     "frac_of_nominal_8TBs": round(achieved / 8000.0, 4)},
+    }
+
+    extra = {}
+    if not args.no_extra:
+        reps = max(5, min(50, args.steps // 4))
+        # decode + sum (compressed bytes only)
+        sums = torch.zeros(L, dtype=torch.int64, device="cuda")
+        ms_sum = time_launches(stream, lambda: batch.sum_into(sums, status, stream), reps, 2)
+        extra["gl_decode_sum_uniform"] = {
+            "gints": round(total_n / (ms_sum * 1e-3) / 1e9, 2), "ms": round(ms_sum, 4),
+            "gbs_compressed": round(comp_bytes / (ms_sum * 1e-3) / 1e9, 1)}
+        # clustered lists
+        cl = make_lists("clustered", L, n, UNIVERSE, seed + 1000)
+        cbatch = api.ListBatch(encode_all(cl, capi.BP_LAYOUT_GPU), [n] * L, capi.BP_LAYOUT_GPU)
+        with torch.cuda.stream(stream):
+            cbatch.decode_into(out, status, stream)
+        stream.synchronize()
+        assert torch.equal(out, torch.from_numpy(np.concatenate(cl).view(np.int32)).to("cuda"))
+        ms_c = time_launches(stream, lambda: cbatch.decode_into(out, status, stream), reps, 2)
+        extra["gl_decode_clustered"] = {
+            "gints": round(total_n / (ms_c * 1e-3) / 1e9, 2), "ms": round(ms_c, 4),
+            "bits_per_int": round(8 * cbatch.compressed_bytes / total_n, 3),
+            "hbm_gbs": round((cbatch.compressed_bytes + 4 * total_n) / (ms_c * 1e-3) / 1e9, 1)}
+        del cbatch, cl
+        # paper layout
+        pbatch = api.ListBatch(encode_all(lists, capi.BP_LAYOUT_PAPER), [n] * L,
+                               capi.BP_LAYOUT_PAPER)
+        with torch.cuda.stream(stream):
+            pbatch.decode_into(out, status, stream)
+        stream.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(out, torch.from_numpy(np.concatenate(lists).view(np.int32)).to("cuda"))
+        ms_p = time_launches(stream, lambda: pbatch.decode_into(out, status, stream),
+                             max(3, reps // 5), 1)
+        extra["pl_decode_uniform"] = {
+            "gints": round(total_n / (ms_p * 1e-3) / 1e9, 2), "ms": round(ms_p, 4),
+            "bits_per_int": round(8 * pbatch.compressed_bytes / total_n, 3)}
+        del pbatch
+    clocks.stop()
+    if extra:
+        result["secondary"] = extra
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    if not args.no_e2e:
+        h_data = torch.from_numpy(batch.host_data).pin_memory()
+        h_lists = torch.from_numpy(batch.lists.view(np.uint8).copy()).pin_memory()
+        h_out = torch.empty(total_n, dtype=torch.int32).pin_memory()
+        h_status = torch.zeros(1, dtype=torch.int32).pin_memory()
+        d_data = torch.empty_like(batch.data)
+        d_lists = torch.empty_like(batch.d_lists)
+
+        def e2e_step():
+            capi.check(capi.bp_decode_batch_host(
+                h_data.data_ptr(), h_data.numel(), h_lists.data_ptr(), L, batch.total_units,
+                capi.BP_LAYOUT_GPU, d_data.data_ptr(), d_lists.data_ptr(), out.data_ptr(),
+                total_n, h_out.data_ptr(), batch.scratch.data_ptr(), batch.scratch_bytes,
+                status.data_ptr(), h_status.data_ptr(), stream.cuda_stream), "e2e")
+
+        e2e_steps = max(3, min(20, args.steps // 10))
+        barrier(dist)
+        ms_e = time_launches(stream, e2e_step, e2e_steps, 2)
+        ms_e = max_over_ranks(dist, ms_e)
+        assert int(h_status.item()) == 0
+        assert np.array_equal(h_out[:1000].numpy().view(np.uint32), lists[0][:1000])
+        result["e2e"] = {"value": round(world * total_n / (ms_e * 1e-3) / 1e9, 3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(h_data.numel() + h_lists.numel()),
+                         "d2h_bytes_per_step": int(4 * total_n + 4),
+                         "ms_per_step": round(ms_e, 3), "steps": e2e_steps,
+                         "call": "bp_decode_batch_host"}
+
+    # the oracle on the host cores, rank 0 at N = 1 only
+    if world == 1 and rank == 0 and not args.no_cpu:
+        threads = min(16, os.cpu_count() or 1)
+        k = min(L, 16)
+        val, dt, used = oracle_decode_rate(encs[:k], [n] * k, threads)
+        result["cpu_baseline"] = {
+            "value": round(val, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{k} of the {L} GL-encoded lists (2^{args.log2n} ints each) decoded by "
+                      f"the scalar C oracle on {used} threads, {dt:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -83,6 +83,29 @@ typedef struct bp_list {
   uint64_t reserved;
 } bp_list;
 
+/* Intersection modes of bp_intersect_pair. */
+typedef enum {
+  BP_MODE_AUTO = 0,    /* fused for BP_LAYOUT_GPU, unfused for the paper layout */
+  BP_MODE_UNFUSED = 1, /* decode both lists to scratch, intersect the arrays    */
+  BP_MODE_FUSED = 2    /* BP_LAYOUT_GPU only: decode only candidate blocks      */
+} bp_mode;
+
+/* Tuning parameters (process-wide; bp_set_tuning installs the autotuner's
+ * choice).  dense_blocks is the skew threshold between the two regimes of
+ * Section 6: a 128-value chunk of the shorter list whose range covers at
+ * most dense_blocks blocks of the longer list decodes them all and searches
+ * them (similar lengths, the V1/V3 regime); a wider range decodes only the
+ * blocks that some value falls in, found by binary search over the skip
+ * headers (skewed lengths, the galloping regime).  query_chunk_blocks is the
+ * number of blocks of a query's shortest list per work item in
+ * bp_query_batch, query_warps the warps per CTA of its persistent kernel. */
+typedef struct bp_tuning {
+  uint32_t dense_blocks;       /* 1..8, default 4 */
+  uint32_t query_chunk_blocks; /* 1..8, default 1 */
+  uint32_t query_warps;        /* 4 or 8, default 8 */
+  uint32_t reserved[5];
+} bp_tuning;
+
 /* Status text for a bp_status code (static string, never NULL). */
 const char *bp_status_string(int status);
 
@@ -148,6 +171,45 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists,
                     uint32_t *d_out, uint64_t out_cap, uint64_t *d_sums,
                     void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
                     void *stream);
+
+/* bp_decode_batch from and to host memory, for callers that keep the
+ * compressed lists on the host: enqueues on `stream` the copy of h_data
+ * (data_bytes) to d_data and of h_lists (count planned descriptors) to
+ * d_lists, a reset of *d_status, the decode, and the copies of the decoded
+ * lists (sum of n over the lists, as uint32) to h_out and of the status to
+ * *h_status.  Host buffers should be pinned for the copies to be
+ * asynchronous; all buffers belong to the caller and must stay alive until
+ * the stream has passed the call.  Layout, scratch and errors as in
+ * bp_decode_batch (sums are not offered here). */
+int bp_decode_batch_host(const uint8_t *h_data, size_t data_bytes,
+                         const bp_list *h_lists, uint32_t count,
+                         uint64_t total_units, int layout, uint8_t *d_data,
+                         bp_list *d_lists, uint32_t *d_out, uint64_t out_cap,
+                         uint32_t *h_out, void *d_scratch, size_t scratch_bytes,
+                         uint32_t *d_status, uint32_t *h_status, void *stream);
+
+/* Current tuning parameters / install new ones (BP_ERR_ARG if out of
+ * range).  Calls already enqueued keep the values they were launched with. */
+int bp_get_tuning(bp_tuning *out);
+int bp_set_tuning(const bp_tuning *in);
+
+/* Scratch needed by bp_intersect_pair for lists of n_a and n_b integers. */
+size_t bp_intersect_scratch_bytes(size_t n_a, size_t n_b, int layout, int mode);
+
+/* Sorted intersection of two compressed lists of distinct sorted integers
+ * (Section 6: the shorter list r is searched in the longer list f; the
+ * result is the values of r found in f, ascending).  Streams as in
+ * bp_decode (device, 16-byte aligned, n checked against the header).
+ * Writes min(count, out_cap) values to d_out and the count to *d_count
+ * (device uint32); count > out_cap records BP_ERR_CAPACITY (out_cap >=
+ * min(n_a, n_b) always suffices).  mode: bp_mode; BP_MODE_FUSED needs
+ * BP_LAYOUT_GPU (else BP_ERR_ARG).  Scratch: bp_intersect_scratch_bytes;
+ * the call enqueues a memset of part of it. */
+int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a,
+                      const uint8_t *d_b, size_t b_bytes, size_t n_b,
+                      int layout, int mode, uint32_t *d_out, size_t out_cap,
+                      uint32_t *d_count, void *d_scratch, size_t scratch_bytes,
+                      uint32_t *d_status, void *stream);
 
 #ifdef __cplusplus
 }

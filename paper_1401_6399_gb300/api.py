@@ -29,7 +29,8 @@ def check_status(status: torch.Tensor, what: str) -> None:
 def to_device(enc: np.ndarray, device="cuda") -> torch.Tensor:
     """Copy an encoded stream (uint8) to the device (torch allocations are
     256-byte aligned, which meets the 16-byte rule of the ABI)."""
-    t = torch.from_numpy(np.ascontiguousarray(enc, np.uint8))
+    a = np.ascontiguousarray(enc, np.uint8)
+    t = torch.from_numpy(a if a.flags.writeable else a.copy())
     return t.to(device, non_blocking=False)
 
 
@@ -120,3 +121,25 @@ class ListBatch:
         self.sum_into(s, st)
         check_status(st, "bp_decode_batch")
         return s.cpu().numpy().view(np.uint64)
+
+
+def intersect_pair(a_dev: torch.Tensor, n_a: int, b_dev: torch.Tensor, n_b: int,
+                   layout: int = capi.BP_LAYOUT_GPU, mode: int = capi.BP_MODE_AUTO,
+                   stream=None) -> torch.Tensor:
+    """Sorted intersection of two device-resident compressed lists."""
+    if stream is not None:
+        with torch.cuda.stream(stream):
+            return intersect_pair(a_dev, n_a, b_dev, n_b, layout, mode)
+    dev = a_dev.device
+    cap = max(1, min(n_a, n_b))
+    out = torch.empty(cap, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    sb = capi.bp_intersect_scratch_bytes(n_a, n_b, layout, mode)
+    scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=dev)
+    st = status_tensor(dev)
+    check(capi.bp_intersect_pair(a_dev.data_ptr(), a_dev.numel(), n_a, b_dev.data_ptr(),
+                                 b_dev.numel(), n_b, layout, mode, out.data_ptr(), cap,
+                                 cnt.data_ptr(), scratch.data_ptr(), sb, st.data_ptr(),
+                                 _stream(None)), "bp_intersect_pair")
+    check_status(st, "bp_intersect_pair")
+    return out[: int(cnt.item())]

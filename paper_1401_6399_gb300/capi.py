@@ -16,6 +16,12 @@ from .build import LIB
 BP_OK, BP_ERR_ARG, BP_ERR_UNSORTED, BP_ERR_CORRUPT = 0, 1, 2, 3
 BP_ERR_CAPACITY, BP_ERR_CUDA, BP_ERR_TIMEOUT, BP_ERR_SCRATCH = 4, 5, 6, 7
 BP_LAYOUT_PAPER, BP_LAYOUT_GPU = 0, 1
+BP_MODE_AUTO, BP_MODE_UNFUSED, BP_MODE_FUSED = 0, 1, 2
+
+
+class bp_tuning(C.Structure):
+    _fields_ = [("dense_blocks", C.c_uint32), ("query_chunk_blocks", C.c_uint32),
+                ("query_warps", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
 # struct bp_list (48 bytes)
 BP_LIST = np.dtype([("enc_offset", "<u8"), ("enc_bytes", "<u8"), ("out_offset", "<u8"),
@@ -48,6 +54,13 @@ _decl("bp_decode", _int, _vp, _sz, _int, _sz, _vp, _sz, _vp, _sz, _vp, _vp)
 _decl("bp_decode_sum", _int, _vp, _sz, _int, _sz, _vp, _vp, _sz, _vp, _vp)
 _decl("bp_decode_batch_scratch_bytes", _sz, _vp, _u32)
 _decl("bp_decode_batch", _int, _vp, _vp, _u32, _u64, _int, _vp, _u64, _vp, _vp, _sz, _vp, _vp)
+_decl("bp_decode_batch_host", _int, _vp, _sz, _vp, _u32, _u64, _int, _vp, _vp, _vp, _u64, _vp,
+      _vp, _sz, _vp, _vp, _vp)
+_decl("bp_get_tuning", _int, C.POINTER(bp_tuning))
+_decl("bp_set_tuning", _int, C.POINTER(bp_tuning))
+_decl("bp_intersect_scratch_bytes", _sz, _sz, _sz, _int, _int)
+_decl("bp_intersect_pair", _int, _vp, _sz, _sz, _vp, _sz, _sz, _int, _int, _vp, _sz, _vp, _vp,
+      _sz, _vp, _vp)
 
 
 class BPError(RuntimeError):
@@ -123,3 +136,35 @@ def bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap,
                     d_scratch, scratch_bytes, d_status, stream) -> int:
     return lib.bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap,
                                d_sums, d_scratch, scratch_bytes, d_status, stream)
+
+
+def bp_get_tuning() -> dict:
+    t = bp_tuning()
+    check(lib.bp_get_tuning(C.byref(t)), "bp_get_tuning")
+    return {"dense_blocks": t.dense_blocks, "query_chunk_blocks": t.query_chunk_blocks,
+            "query_warps": t.query_warps}
+
+
+def bp_set_tuning(**kw) -> None:
+    cur = bp_get_tuning()
+    cur.update(kw)
+    t = bp_tuning(cur["dense_blocks"], cur["query_chunk_blocks"], cur["query_warps"])
+    check(lib.bp_set_tuning(C.byref(t)), "bp_set_tuning")
+
+
+def bp_intersect_scratch_bytes(n_a: int, n_b: int, layout: int, mode: int) -> int:
+    return int(lib.bp_intersect_scratch_bytes(n_a, n_b, layout, mode))
+
+
+def bp_intersect_pair(d_a, a_bytes, n_a, d_b, b_bytes, n_b, layout, mode, d_out, out_cap,
+                      d_count, d_scratch, scratch_bytes, d_status, stream) -> int:
+    return lib.bp_intersect_pair(d_a, a_bytes, n_a, d_b, b_bytes, n_b, layout, mode, d_out,
+                                 out_cap, d_count, d_scratch, scratch_bytes, d_status, stream)
+
+
+def bp_decode_batch_host(h_data, data_bytes, h_lists, count, total_units, layout, d_data, d_lists,
+                         d_out, out_cap, h_out, d_scratch, scratch_bytes, d_status, h_status,
+                         stream) -> int:
+    return lib.bp_decode_batch_host(h_data, data_bytes, h_lists, count, total_units, layout,
+                                    d_data, d_lists, d_out, out_cap, h_out, d_scratch,
+                                    scratch_bytes, d_status, h_status, stream)

@@ -1,4 +1,5 @@
 // capi.cu -- extern "C" entry points of the device-side decode calls.
+#include <algorithm>
 #include <mutex>
 
 #include "decode.h"
@@ -94,6 +95,59 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists, uint32_t coun
     return bp::launch_gl_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_status, s);
   return bp::launch_pl_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_scratch,
                               scratch_bytes, d_status, s);
+}
+
+int bp_decode_batch_host(const uint8_t *h_data, size_t data_bytes, const bp_list *h_lists,
+                         uint32_t count, uint64_t total_units, int layout, uint8_t *d_data,
+                         bp_list *d_lists, uint32_t *d_out, uint64_t out_cap, uint32_t *h_out,
+                         void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+                         uint32_t *h_status, void *stream) {
+  if (!h_data || !h_lists || !d_data || !d_lists || !d_out || !h_out || !d_status || !h_status ||
+      count == 0)
+    return BP_ERR_ARG;
+  uint64_t total_n = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    if (h_lists[i].enc_offset + h_lists[i].enc_bytes > data_bytes) return BP_ERR_ARG;
+    total_n = std::max<uint64_t>(total_n, h_lists[i].out_offset + h_lists[i].n);
+  }
+  if (total_n > out_cap) return BP_ERR_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(d_data, h_data, data_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_lists, h_lists, sizeof(bp_list) * count, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess)
+    return BP_ERR_CUDA;
+  int rc = bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap, nullptr,
+                           d_scratch, scratch_bytes, d_status, stream);
+  if (rc != BP_OK) return rc;
+  if (cudaMemcpyAsync(h_out, d_out, 4ull * total_n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess)
+    return BP_ERR_CUDA;
+  return BP_OK;
+}
+
+size_t bp_intersect_scratch_bytes(size_t n_a, size_t n_b, int layout, int mode) {
+  if (mode == BP_MODE_AUTO) mode = layout == BP_LAYOUT_GPU ? BP_MODE_FUSED : BP_MODE_UNFUSED;
+  return bp::intersect_scratch_bytes(n_a, n_b, layout, mode);
+}
+
+int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a, const uint8_t *d_b,
+                      size_t b_bytes, size_t n_b, int layout, int mode, uint32_t *d_out,
+                      size_t out_cap, uint32_t *d_count, void *d_scratch, size_t scratch_bytes,
+                      uint32_t *d_status, void *stream) {
+  if (!d_a || !d_b || !d_count || !d_status || !d_scratch) return BP_ERR_ARG;
+  if (!aligned16(d_a) || !aligned16(d_b)) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (n_a > bp_fmt::kMaxList || n_b > bp_fmt::kMaxList) return BP_ERR_ARG;
+  if (mode == BP_MODE_AUTO) mode = layout == BP_LAYOUT_GPU ? BP_MODE_FUSED : BP_MODE_UNFUSED;
+  if (mode != BP_MODE_FUSED && mode != BP_MODE_UNFUSED) return BP_ERR_ARG;
+  if (mode == BP_MODE_FUSED && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (!d_out && out_cap) return BP_ERR_ARG;
+  if (scratch_bytes < bp::intersect_scratch_bytes(n_a, n_b, layout, mode)) return BP_ERR_SCRATCH;
+  return bp::launch_intersect_pair(d_a, a_bytes, n_a, d_b, b_bytes, n_b, layout, mode, d_out,
+                                   out_cap, d_count, d_scratch, scratch_bytes, d_status,
+                                   static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -55,4 +55,11 @@ int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
                      uint32_t *out, uint64_t out_cap, uint64_t *sums, void *scratch,
                      size_t scratch_bytes, uint32_t *status, cudaStream_t s);
 
+// Pairwise intersection (intersect.cu).
+size_t intersect_scratch_bytes(size_t na, size_t nb, int layout, int mode);
+int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const uint8_t *db,
+                          size_t b_bytes, size_t nb, int layout, int mode, uint32_t *out,
+                          size_t out_cap, uint32_t *count, void *scratch, size_t scratch_bytes,
+                          uint32_t *status, cudaStream_t s);
+
 }  // namespace bp

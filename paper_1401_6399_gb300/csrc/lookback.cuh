@@ -1,0 +1,71 @@
+// lookback.cuh -- single-pass ordered compaction across CTAs: every tile
+// takes a ticket (so tiles start in order and a tile only ever waits on
+// tiles that are already running), publishes its count, then looks back
+// over earlier tiles for the number of outputs before it.
+//
+// Tile state word (u64): flag << 32 | value; flag 1 = the tile's own count,
+// 2 = inclusive count of all tiles up to it.  The words and the ticket live
+// in caller scratch and are zeroed by the host before each launch.  Every
+// wait is bounded: after kSpinLimit polls it records BP_ERR_TIMEOUT and
+// proceeds as if the missing tile had no output.
+#pragma once
+#include "common.cuh"
+
+namespace bp {
+
+constexpr uint32_t kLookbackSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Called by one thread of tile t with the tile's own count; returns the
+// number of outputs of tiles 0..t-1.
+__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *state, uint32_t t, uint32_t agg,
+                                                      uint32_t *status) {
+  if (t == 0) {
+    st_release_u64(state, (2ull << 32) | agg);
+    return 0;
+  }
+  st_release_u64(state + t, (1ull << 32) | agg);
+  uint32_t excl = 0;
+  for (int64_t j = (int64_t)t - 1; j >= 0; j--) {
+    uint64_t s;
+    uint32_t spins = 0;
+    while (((s = ld_acquire_u64(state + j)) >> 32) == 0) {
+      if (++spins > kLookbackSpinLimit) break;
+      __nanosleep(64);
+    }
+    if ((s >> 32) == 0) {
+      set_status(status, BP_ERR_TIMEOUT);
+      break;
+    }
+    excl += (uint32_t)s;
+    if ((s >> 32) == 2) break;
+  }
+  st_release_u64(state + t, (2ull << 32) | (excl + agg));
+  return excl;
+}
+
+// Scratch of one compaction: ticket counter + one state word per tile.
+struct Compaction {
+  uint32_t *ticket;
+  uint64_t *state;
+};
+
+__host__ __device__ inline size_t compaction_bytes(uint64_t ntiles) { return 16 + 8 * ntiles; }
+
+inline Compaction compaction_at(void *p) {
+  Compaction c;
+  c.ticket = static_cast<uint32_t *>(p);
+  c.state = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(p) + 16);
+  return c;
+}
+
+}  // namespace bp
