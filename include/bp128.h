@@ -127,6 +127,17 @@ int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
 int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
                    int *layout_out);
 
+/* Index builder: encode `count` lists (list i = values[offs[i] ..
+ * offs[i+1]), strictly increasing) in BP_LAYOUT_GPU back to back into out
+ * (each stream 16-byte aligned, cap bytes; bp_index_bound gives enough) and
+ * fill lists[i] (enc_offset, enc_bytes, out_offset = offs[i], n, layout,
+ * unit_base as bp_plan_lists).  *out_bytes: bytes used.  Errors as
+ * bp_encode.  nthreads host threads share the lists. */
+size_t bp_index_bound(const uint64_t *offs, uint32_t count);
+int bp_index_encode(const uint32_t *values, const uint64_t *offs,
+                    uint32_t count, uint8_t *out, size_t cap, bp_list *lists,
+                    size_t *out_bytes, int nthreads);
+
 /* Fill lists[i].unit_base for a batch of `count` lists of one layout and
  * return the total number of work units (GL: groups of 32 blocks; PL: blocks
  * of 128 integers plus one unit for each list's tail). */
@@ -210,6 +221,53 @@ int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a,
                       int layout, int mode, uint32_t *d_out, size_t out_cap,
                       uint32_t *d_count, void *d_scratch, size_t scratch_bytes,
                       uint32_t *d_status, void *stream);
+
+/* ---- conjunctive queries over a resident index -------------------------- *
+ * The index is a device buffer d_data holding one GL stream per term
+ * (16-byte aligned) and a device array d_lists of n_terms descriptors
+ * (enc_offset, enc_bytes, n; the other fields are ignored).  A query is a
+ * set of term ids; its answer is the sorted intersection of their lists
+ * (Section 6, Set-vs-Set from the shortest list; P:196, 967 of the paper). */
+
+/* Scratch needed by bp_query_batch; host copies of the index descriptors
+ * and of the queries' terms, out_cap as passed to bp_query_batch. */
+size_t bp_query_batch_scratch_bytes(const bp_list *h_lists, uint32_t n_terms,
+                                    const uint32_t *h_terms,
+                                    const uint64_t *h_term_off,
+                                    uint32_t n_queries, uint64_t out_cap);
+
+/* Answer n_queries queries in one pass: query q has the terms
+ * d_terms[d_term_off[q] .. d_term_off[q+1]) (at most 64; device arrays,
+ * total_terms = d_term_off[n_queries]).  The answers are written back to
+ * back in query order to d_out (out_cap uint32 in total): query q's answer
+ * starts at d_out_off[q] (device uint64, n_queries+1 entries) and has
+ * d_counts[q] values (device uint32).  A total beyond out_cap, or beyond the
+ * work items the scratch holds, records BP_ERR_CAPACITY / BP_ERR_SCRATCH;
+ * counts and offsets stay exact.  An unknown term id records BP_ERR_ARG.
+ * Every launch size depends only on n_queries and the buffers, so the call
+ * can be captured in a CUDA graph and replayed with new terms in the same
+ * device arrays. */
+int bp_query_batch(const uint8_t *d_data, const bp_list *d_lists,
+                   uint32_t n_terms, const uint32_t *d_terms,
+                   const uint64_t *d_term_off, uint64_t total_terms,
+                   uint32_t n_queries, uint32_t *d_out, uint64_t out_cap,
+                   uint64_t *d_out_off, uint32_t *d_counts, void *d_scratch,
+                   size_t scratch_bytes, uint32_t *d_status, void *stream);
+
+/* Scratch needed by bp_query_one for the k terms h_terms. */
+size_t bp_query_one_scratch_bytes(const bp_list *h_lists, uint32_t n_terms,
+                                  const uint32_t *h_terms, uint32_t k);
+
+/* One query, the plain way: every list of the query is decoded whole into
+ * scratch, then the decoded arrays are intersected two at a time from the
+ * shortest (decompress-then-intersect, Section 7.6 of the paper).  h_lists:
+ * host copy of the descriptors; h_terms: k host term ids.  Answer in
+ * d_out[0..count), count in *d_count (device). */
+int bp_query_one(const uint8_t *d_data, const bp_list *h_lists,
+                 uint32_t n_terms, const uint32_t *h_terms, uint32_t k,
+                 uint32_t *d_out, size_t out_cap, uint32_t *d_count,
+                 void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+                 void *stream);
 
 #ifdef __cplusplus
 }

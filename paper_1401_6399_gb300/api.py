@@ -143,3 +143,77 @@ def intersect_pair(a_dev: torch.Tensor, n_a: int, b_dev: torch.Tensor, n_b: int,
                                  _stream(None)), "bp_intersect_pair")
     check_status(st, "bp_intersect_pair")
     return out[: int(cnt.item())]
+
+
+class Index:
+    """A resident index: one GL stream per term in one device buffer, the
+    descriptors on host and device, and the query calls over it."""
+
+    def __init__(self, values: np.ndarray, offs: np.ndarray, device="cuda", nthreads: int = 16):
+        host, lists = capi.bp_index_encode(values, offs, nthreads)
+        self.h_lists = lists
+        self.n_terms = lists.size
+        self.host_data = host
+        self.data = to_device(host, device)
+        self.d_lists = torch.from_numpy(lists.view(np.uint8).copy()).to(device)
+        self.compressed_bytes = int(host.size)
+        self.device = device
+
+    def lengths(self) -> np.ndarray:
+        return self.h_lists["n"].astype(np.uint64)
+
+    def query_batch_async(self, d_terms: torch.Tensor, d_term_off: torch.Tensor, nq: int,
+                          total_terms: int, out: torch.Tensor, out_off: torch.Tensor,
+                          counts: torch.Tensor, scratch: torch.Tensor, status: torch.Tensor,
+                          stream=None) -> None:
+        check(capi.bp_query_batch(self.data.data_ptr(), self.d_lists.data_ptr(), self.n_terms,
+                                  d_terms.data_ptr() if total_terms else None,
+                                  d_term_off.data_ptr(), total_terms, nq, out.data_ptr(),
+                                  out.numel(), out_off.data_ptr(), counts.data_ptr(),
+                                  scratch.data_ptr(), scratch.numel(), status.data_ptr(),
+                                  _stream(stream)), "bp_query_batch")
+
+    def query_batch(self, terms: np.ndarray, term_off: np.ndarray, out_cap: int | None = None):
+        """Answer all queries; returns a list of uint32 arrays."""
+        terms = np.ascontiguousarray(terms, np.uint32)
+        term_off = np.ascontiguousarray(term_off, np.uint64)
+        nq = term_off.size - 1
+        if out_cap is None:
+            lens = self.h_lists["n"]
+            out_cap = 0
+            for q in range(nq):
+                t = terms[term_off[q]:term_off[q + 1]]
+                out_cap += int(lens[t].min()) if t.size else 0
+        out_cap = max(out_cap, 1)
+        sb = capi.bp_query_batch_scratch_bytes(self.h_lists, terms, term_off, out_cap)
+        dev = self.device
+        d_terms = torch.from_numpy(terms.view(np.int32).copy() if terms.size else
+                                   np.zeros(1, np.int32)).to(dev)
+        d_off = torch.from_numpy(term_off.view(np.int64).copy()).to(dev)
+        out = torch.empty(out_cap, dtype=torch.int32, device=dev)
+        out_off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+        counts = torch.empty(max(nq, 1), dtype=torch.int32, device=dev)
+        scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=dev)
+        st = status_tensor(dev)
+        self.query_batch_async(d_terms, d_off, nq, int(term_off[-1]), out, out_off, counts,
+                               scratch, st)
+        check_status(st, "bp_query_batch")
+        o = out_off.cpu().numpy().view(np.uint64)
+        c = counts.cpu().numpy().view(np.uint32)
+        flat = as_u32(out[: int(o[nq])]) if nq else np.zeros(0, np.uint32)
+        return [flat[int(o[q]):int(o[q]) + int(c[q])] for q in range(nq)]
+
+    def query_one(self, terms, stream=None) -> torch.Tensor:
+        terms = np.ascontiguousarray(terms, np.uint32)
+        dev = self.device
+        cap = max(1, int(self.h_lists["n"][terms].min()) if terms.size else 1)
+        out = torch.empty(cap, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        sb = capi.bp_query_one_scratch_bytes(self.h_lists, terms)
+        scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=dev)
+        st = status_tensor(dev)
+        check(capi.bp_query_one(self.data.data_ptr(), self.h_lists, terms, out.data_ptr(), cap,
+                                cnt.data_ptr(), scratch.data_ptr(), sb, st.data_ptr(),
+                                _stream(stream)), "bp_query_one")
+        check_status(st, "bp_query_one")
+        return out[: int(cnt.item())]

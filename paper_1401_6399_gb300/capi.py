@@ -49,6 +49,8 @@ _decl("bp_encode_bound", _sz, _sz, _int)
 _decl("bp_encode", _int, _vp, _sz, _int, _vp, _sz, C.POINTER(_sz), _int)
 _decl("bp_stream_info", _int, _vp, _sz, C.POINTER(_u32), C.POINTER(_int))
 _decl("bp_plan_lists", _u64, _vp, _u32)
+_decl("bp_index_bound", _sz, _vp, _u32)
+_decl("bp_index_encode", _int, _vp, _vp, _u32, _vp, _sz, _vp, C.POINTER(_sz), _int)
 _decl("bp_decode_scratch_bytes", _sz, _sz, _int)
 _decl("bp_decode", _int, _vp, _sz, _int, _sz, _vp, _sz, _vp, _sz, _vp, _vp)
 _decl("bp_decode_sum", _int, _vp, _sz, _int, _sz, _vp, _vp, _sz, _vp, _vp)
@@ -56,6 +58,11 @@ _decl("bp_decode_batch_scratch_bytes", _sz, _vp, _u32)
 _decl("bp_decode_batch", _int, _vp, _vp, _u32, _u64, _int, _vp, _u64, _vp, _vp, _sz, _vp, _vp)
 _decl("bp_decode_batch_host", _int, _vp, _sz, _vp, _u32, _u64, _int, _vp, _vp, _vp, _u64, _vp,
       _vp, _sz, _vp, _vp, _vp)
+_decl("bp_query_batch_scratch_bytes", _sz, _vp, _u32, _vp, _vp, _u32, _u64)
+_decl("bp_query_batch", _int, _vp, _vp, _u32, _vp, _vp, _u64, _u32, _vp, _u64, _vp, _vp, _vp,
+      _sz, _vp, _vp)
+_decl("bp_query_one_scratch_bytes", _sz, _vp, _u32, _vp, _u32)
+_decl("bp_query_one", _int, _vp, _vp, _u32, _vp, _u32, _vp, _sz, _vp, _vp, _sz, _vp, _vp)
 _decl("bp_get_tuning", _int, C.POINTER(bp_tuning))
 _decl("bp_set_tuning", _int, C.POINTER(bp_tuning))
 _decl("bp_intersect_scratch_bytes", _sz, _sz, _sz, _int, _int)
@@ -107,6 +114,21 @@ def bp_stream_info(enc) -> tuple[int, int]:
 def bp_plan_lists(lists: np.ndarray) -> int:
     assert lists.dtype == BP_LIST and lists.flags.c_contiguous
     return int(lib.bp_plan_lists(lists.ctypes.data, lists.size))
+
+
+def bp_index_encode(values: np.ndarray, offs: np.ndarray, nthreads: int = 8):
+    """Encode many lists into one GL buffer; returns (uint8 buffer, BP_LIST array)."""
+    values = np.ascontiguousarray(values, np.uint32)
+    offs = np.ascontiguousarray(offs, np.uint64)
+    count = offs.size - 1
+    cap = int(lib.bp_index_bound(offs.ctypes.data, count))
+    out = np.empty(max(cap, 16), np.uint8)
+    lists = np.zeros(count, BP_LIST)
+    used = _sz(0)
+    check(lib.bp_index_encode(values.ctypes.data if values.size else None, offs.ctypes.data,
+                              count, out.ctypes.data, cap, lists.ctypes.data, C.byref(used),
+                              nthreads), "bp_index_encode")
+    return out[: max(used.value, 16)], lists
 
 
 # ---- device (raw pointers) ---------------------------------------------------------
@@ -168,3 +190,35 @@ def bp_decode_batch_host(h_data, data_bytes, h_lists, count, total_units, layout
     return lib.bp_decode_batch_host(h_data, data_bytes, h_lists, count, total_units, layout,
                                     d_data, d_lists, d_out, out_cap, h_out, d_scratch,
                                     scratch_bytes, d_status, h_status, stream)
+
+
+def bp_query_batch_scratch_bytes(h_lists: np.ndarray, h_terms: np.ndarray,
+                                 h_term_off: np.ndarray, out_cap: int) -> int:
+    assert h_lists.dtype == BP_LIST
+    h_terms = np.ascontiguousarray(h_terms, np.uint32)
+    h_term_off = np.ascontiguousarray(h_term_off, np.uint64)
+    return int(lib.bp_query_batch_scratch_bytes(
+        h_lists.ctypes.data, h_lists.size, h_terms.ctypes.data if h_terms.size else None,
+        h_term_off.ctypes.data, h_term_off.size - 1, out_cap))
+
+
+def bp_query_batch(d_data, d_lists, n_terms, d_terms, d_term_off, total_terms, n_queries, d_out,
+                   out_cap, d_out_off, d_counts, d_scratch, scratch_bytes, d_status,
+                   stream) -> int:
+    return lib.bp_query_batch(d_data, d_lists, n_terms, d_terms, d_term_off, total_terms,
+                              n_queries, d_out, out_cap, d_out_off, d_counts, d_scratch,
+                              scratch_bytes, d_status, stream)
+
+
+def bp_query_one_scratch_bytes(h_lists: np.ndarray, terms) -> int:
+    t = np.ascontiguousarray(terms, np.uint32)
+    return int(lib.bp_query_one_scratch_bytes(h_lists.ctypes.data, h_lists.size,
+                                              t.ctypes.data if t.size else None, t.size))
+
+
+def bp_query_one(d_data, h_lists: np.ndarray, terms, d_out, out_cap, d_count, d_scratch,
+                 scratch_bytes, d_status, stream) -> int:
+    t = np.ascontiguousarray(terms, np.uint32)
+    return lib.bp_query_one(d_data, h_lists.ctypes.data, h_lists.size,
+                            t.ctypes.data if t.size else None, t.size, d_out, out_cap, d_count,
+                            d_scratch, scratch_bytes, d_status, stream)

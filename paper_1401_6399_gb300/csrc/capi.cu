@@ -150,4 +150,45 @@ int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a, const uint
                                    static_cast<cudaStream_t>(stream));
 }
 
+size_t bp_query_batch_scratch_bytes(const bp_list *h_lists, uint32_t n_terms,
+                                    const uint32_t *h_terms, const uint64_t *h_term_off,
+                                    uint32_t n_queries, uint64_t out_cap) {
+  if (!h_term_off || (n_terms && !h_lists)) return 0;
+  return bp::query_batch_scratch_bytes(h_lists, n_terms, h_terms, h_term_off, n_queries, out_cap);
+}
+
+int bp_query_batch(const uint8_t *d_data, const bp_list *d_lists, uint32_t n_terms,
+                   const uint32_t *d_terms, const uint64_t *d_term_off, uint64_t total_terms,
+                   uint32_t n_queries, uint32_t *d_out, uint64_t out_cap, uint64_t *d_out_off,
+                   uint32_t *d_counts, void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+                   void *stream) {
+  if (!d_data || !d_lists || !d_term_off || !d_out_off || !d_counts || !d_status || !d_scratch)
+    return BP_ERR_ARG;
+  if ((total_terms && !d_terms) || (out_cap && !d_out) || !aligned16(d_data)) return BP_ERR_ARG;
+  return bp::launch_query_batch(d_data, d_lists, n_terms, d_terms, d_term_off, total_terms,
+                                n_queries, d_out, out_cap, d_out_off, d_counts, d_scratch,
+                                scratch_bytes, d_status, static_cast<cudaStream_t>(stream));
+}
+
+size_t bp_query_one_scratch_bytes(const bp_list *h_lists, uint32_t n_terms,
+                                  const uint32_t *h_terms, uint32_t k) {
+  if (!h_lists || (k && !h_terms)) return 0;
+  for (uint32_t i = 0; i < k; i++)
+    if (h_terms[i] >= n_terms) return 0;
+  return bp::query_one_scratch_bytes(h_lists, h_terms, k);
+}
+
+int bp_query_one(const uint8_t *d_data, const bp_list *h_lists, uint32_t n_terms,
+                 const uint32_t *h_terms, uint32_t k, uint32_t *d_out, size_t out_cap,
+                 uint32_t *d_count, void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
+                 void *stream) {
+  if (!d_data || !h_lists || !d_count || !d_status || !d_scratch || (k && !h_terms))
+    return BP_ERR_ARG;
+  if (!aligned16(d_data) || k > 64) return BP_ERR_ARG;
+  for (uint32_t i = 0; i < k; i++)
+    if (h_terms[i] >= n_terms) return BP_ERR_ARG;
+  return bp::launch_query_one(d_data, h_lists, h_terms, k, d_out, out_cap, d_count, d_scratch,
+                              scratch_bytes, d_status, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

@@ -62,4 +62,17 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
                           size_t out_cap, uint32_t *count, void *scratch, size_t scratch_bytes,
                           uint32_t *status, cudaStream_t s);
 
+// Conjunctive queries (query.cu).
+size_t query_batch_scratch_bytes(const bp_list *h_lists, uint32_t n_terms, const uint32_t *h_terms,
+                                 const uint64_t *h_term_off, uint32_t nq, uint64_t out_cap);
+int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_terms,
+                       const uint32_t *terms, const uint64_t *term_off, uint64_t total_terms,
+                       uint32_t nq, uint32_t *out, uint64_t out_cap, uint64_t *out_off,
+                       uint32_t *counts, void *scratch, size_t scratch_bytes, uint32_t *status,
+                       cudaStream_t s);
+size_t query_one_scratch_bytes(const bp_list *h_lists, const uint32_t *h_terms, uint32_t k);
+int launch_query_one(const uint8_t *data, const bp_list *h_lists, const uint32_t *h_terms,
+                     uint32_t k, uint32_t *out, uint64_t out_cap, uint32_t *count, void *scratch,
+                     size_t scratch_bytes, uint32_t *status, cudaStream_t s);
+
 }  // namespace bp

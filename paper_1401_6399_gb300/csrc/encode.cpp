@@ -192,9 +192,72 @@ int encode_gpu(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
   return BP_OK;
 }
 
+// Exact GL size of list x[0..n) (needs its block widths).
+size_t gl_size(const uint32_t *x, size_t n) {
+  const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(n);
+  uint64_t w = 0;
+  uint32_t d[128];
+  for (size_t k = 0; k < g.nblocks; k++) {
+    gl_deltas(x, n, k, d);
+    uint32_t m = 0;
+    for (unsigned i = 0; i < 128; i++) m |= d[i];
+    w += 4 * width_of(m);
+  }
+  return g.off_payload + 4 * (size_t)w;
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t bp_index_bound(const uint64_t *offs, uint32_t count) {
+  size_t total = 0;
+  for (uint32_t i = 0; i < count; i++)
+    total += bp_fmt::up16(bp_encode_bound(offs[i + 1] - offs[i], BP_LAYOUT_GPU));
+  return total;
+}
+
+int bp_index_encode(const uint32_t *values, const uint64_t *offs, uint32_t count, uint8_t *out,
+                    size_t cap, bp_list *lists, size_t *out_bytes, int nthreads) {
+  if (!values || !offs || !out || !lists || !out_bytes) return BP_ERR_ARG;
+  std::vector<size_t> sizes(count);
+  std::vector<int> bad(count, 0);
+  parallel_ranges(count, nthreads, [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; i++) {
+      const uint32_t *x = values + offs[i];
+      const size_t n = offs[i + 1] - offs[i];
+      if (n > bp_fmt::kMaxList) bad[i] = BP_ERR_ARG;
+      for (size_t j = 1; j < n && !bad[i]; j++)
+        if (x[j] <= x[j - 1]) bad[i] = BP_ERR_UNSORTED;
+      if (!bad[i]) sizes[i] = gl_size(x, n);
+    }
+  });
+  size_t pos = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    if (bad[i]) return bad[i];
+    lists[i] = bp_list{pos, sizes[i], offs[i], 0, (uint32_t)(offs[i + 1] - offs[i]),
+                       (uint32_t)BP_LAYOUT_GPU, 0};
+    pos += bp_fmt::up16(sizes[i]);
+  }
+  if (pos > cap) return BP_ERR_CAPACITY;
+  bp_plan_lists(lists, count);
+  std::vector<int> rc(count, BP_OK);
+  parallel_ranges(count, nthreads, [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; i++) {
+      size_t got = 0;
+      const size_t n = offs[i + 1] - offs[i];
+      rc[i] = encode_gpu(values + offs[i], n, out + lists[i].enc_offset,
+                         bp_encode_bound(n, BP_LAYOUT_GPU), &got, 1);
+      if (rc[i] == BP_OK && got != sizes[i]) rc[i] = BP_ERR_ARG;
+      const size_t pad = bp_fmt::up16(sizes[i]) - sizes[i];
+      if (pad) std::memset(out + lists[i].enc_offset + sizes[i], 0, pad);
+    }
+  });
+  for (uint32_t i = 0; i < count; i++)
+    if (rc[i] != BP_OK) return rc[i];
+  *out_bytes = pos;
+  return BP_OK;
+}
 
 size_t bp_encode_bound(size_t n, int layout) {
   if (layout == BP_LAYOUT_PAPER) {
