@@ -173,8 +173,11 @@ class Index:
                                   scratch.data_ptr(), scratch.numel(), status.data_ptr(),
                                   _stream(stream)), "bp_query_batch")
 
-    def query_batch(self, terms: np.ndarray, term_off: np.ndarray, out_cap: int | None = None):
-        """Answer all queries; returns a list of uint32 arrays."""
+    def query_batch(self, terms: np.ndarray, term_off: np.ndarray, out_cap: int | None = None,
+                    retry: bool = True, on_device: bool = False):
+        """Answer all queries; returns a list of uint32 arrays.  If the
+        answers overflow out_cap the call is repeated once with the exact
+        total (the counts of a call that ran out of room are still exact)."""
         terms = np.ascontiguousarray(terms, np.uint32)
         term_off = np.ascontiguousarray(term_off, np.uint64)
         nq = term_off.size - 1
@@ -184,23 +187,36 @@ class Index:
             for q in range(nq):
                 t = terms[term_off[q]:term_off[q + 1]]
                 out_cap += int(lens[t].min()) if t.size else 0
-        out_cap = max(out_cap, 1)
-        sb = capi.bp_query_batch_scratch_bytes(self.h_lists, terms, term_off, out_cap)
+        out_cap = max(int(out_cap), 1)
         dev = self.device
         d_terms = torch.from_numpy(terms.view(np.int32).copy() if terms.size else
                                    np.zeros(1, np.int32)).to(dev)
         d_off = torch.from_numpy(term_off.view(np.int64).copy()).to(dev)
-        out = torch.empty(out_cap, dtype=torch.int32, device=dev)
         out_off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
         counts = torch.empty(max(nq, 1), dtype=torch.int32, device=dev)
-        scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=dev)
-        st = status_tensor(dev)
-        self.query_batch_async(d_terms, d_off, nq, int(term_off[-1]), out, out_off, counts,
-                               scratch, st)
-        check_status(st, "bp_query_batch")
+        for attempt in range(2):
+            sb = capi.bp_query_batch_scratch_bytes(self.h_lists, terms, term_off, out_cap)
+            out = torch.empty(out_cap, dtype=torch.int32, device=dev)
+            scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=dev)
+            st = status_tensor(dev)
+            self.query_batch_async(d_terms, d_off, nq, int(term_off[-1]), out, out_off, counts,
+                                   scratch, st)
+            code = int(st.item())
+            total = int(out_off[nq].item()) if nq else 0
+            del scratch
+            if code == capi.BP_ERR_CAPACITY and retry and attempt == 0 and total > out_cap:
+                out_cap = total
+                del out
+                continue
+            if code != capi.BP_OK:
+                raise capi.BPError(code, "bp_query_batch")
+            break
+        self.last_total = total
         o = out_off.cpu().numpy().view(np.uint64)
         c = counts.cpu().numpy().view(np.uint32)
-        flat = as_u32(out[: int(o[nq])]) if nq else np.zeros(0, np.uint32)
+        if on_device:  # (device answers, offsets, counts)
+            return out[:total], o, c[:nq]
+        flat = as_u32(out[:total]) if nq else np.zeros(0, np.uint32)
         return [flat[int(o[q]):int(o[q]) + int(c[q])] for q in range(nq)]
 
     def query_one(self, terms, stream=None) -> torch.Tensor:

@@ -37,9 +37,9 @@ inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 struct QScratch {
   uint32_t *sorted;    // [total_terms] term ids in SvS order
   uint32_t *base;      // [nq + 1] items per query, scanned in place
-  uint32_t *counters;  // [0] next item, [1] arena top
+  unsigned long long *counters;  // [0] next item, [1] arena top
   uint32_t *item_q;    // [max_items]
-  uint32_t *item_off;  // [max_items] arena offset
+  uint64_t *item_off;  // [max_items] arena offset
   uint32_t *item_cnt;  // [max_items]
   uint32_t *item_pre;  // [max_items] outputs of earlier items of the query
   uint32_t *arena;     // [arena_cap]
@@ -60,7 +60,7 @@ QLayout q_layout(uint64_t total_terms, uint32_t nq, uint64_t arena_cap, uint64_t
   L.item_q = up256(L.arena + 4 * arena_cap);
   L.max_items = max_items;
   L.item_off = up256(L.item_q + 4 * max_items);
-  L.item_cnt = up256(L.item_off + 4 * max_items);
+  L.item_cnt = up256(L.item_off + 8 * max_items);
   L.item_pre = up256(L.item_cnt + 4 * max_items);
   L.total = up256(L.item_pre + 4 * max_items);
   return L;
@@ -70,7 +70,7 @@ QLayout q_layout(uint64_t total_terms, uint32_t nq, uint64_t arena_cap, uint64_t
 QLayout q_layout_fit(uint64_t total_terms, uint32_t nq, uint64_t arena_cap, size_t scratch_bytes) {
   QLayout L = q_layout(total_terms, nq, arena_cap, 0);
   const size_t fixed = L.total + 4 * 256;
-  L = q_layout(total_terms, nq, arena_cap, scratch_bytes > fixed ? (scratch_bytes - fixed) / 16 : 0);
+  L = q_layout(total_terms, nq, arena_cap, scratch_bytes > fixed ? (scratch_bytes - fixed) / 20 : 0);
   return L;
 }
 
@@ -79,9 +79,9 @@ QScratch q_carve(void *p, const QLayout &L) {
   QScratch s;
   s.sorted = reinterpret_cast<uint32_t *>(b + L.sorted);
   s.base = reinterpret_cast<uint32_t *>(b + L.base);
-  s.counters = reinterpret_cast<uint32_t *>(b + L.counters);
+  s.counters = reinterpret_cast<unsigned long long *>(b + L.counters);
   s.item_q = reinterpret_cast<uint32_t *>(b + L.item_q);
-  s.item_off = reinterpret_cast<uint32_t *>(b + L.item_off);
+  s.item_off = reinterpret_cast<uint64_t *>(b + L.item_off);
   s.item_cnt = reinterpret_cast<uint32_t *>(b + L.item_cnt);
   s.item_pre = reinterpret_cast<uint32_t *>(b + L.item_pre);
   s.arena = reinterpret_cast<uint32_t *>(b + L.arena);
@@ -176,7 +176,7 @@ __device__ __forceinline__ bool term_view(const uint8_t *data, const bp_list *li
 
 __global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *__restrict__ lists,
                               const uint64_t *__restrict__ toff, uint32_t nq, QScratch sc,
-                              uint32_t max_items, uint32_t arena_cap, uint32_t chunk,
+                              uint32_t max_items, uint64_t arena_cap, uint32_t chunk,
                               uint32_t dense_max, uint32_t *status) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -190,7 +190,7 @@ __global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *_
   }
   for (;;) {
     uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(sc.counters, 1u);
+    if (lane == 0) item = (uint32_t)atomicAdd(sc.counters, 1ull);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
     const int64_t qq = warp_ubound(sc.base, (uint64_t)nq + 1, item, lane);
@@ -248,16 +248,16 @@ __global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *_
       set_status(status, BP_ERR_CORRUPT);
     }
     __syncwarp();
-    uint32_t off = 0;
-    if (lane == 0 && scount) off = atomicAdd(sc.counters + 1, scount);
+    uint64_t off = 0;
+    if (lane == 0 && scount) off = atomicAdd(sc.counters + 1, (unsigned long long)scount);
     off = __shfl_sync(kFull, off, 0);
-    const bool fits = (uint64_t)off + scount <= arena_cap;
+    const bool fits = off + scount <= arena_cap;
     if (!fits && lane == 0) set_status(status, BP_ERR_CAPACITY);
     if (fits)
       for (uint32_t i = lane; i < scount; i += 32) sc.arena[off + i] = s_stage[i];
     if (lane == 0) {
       sc.item_q[item] = q;
-      sc.item_off[item] = fits ? off : 0xFFFFFFFFu;
+      sc.item_off[item] = fits ? off : ~0ull;
       sc.item_cnt[item] = scount;
     }
     __syncwarp();
@@ -340,8 +340,9 @@ __global__ void q_gather_kernel(QScratch sc, uint32_t nq, uint32_t max_items,
   const uint32_t total = sc.base[nq];
   if (total > max_items) return;
   for (uint64_t item = warp; item < total; item += nwarps) {
-    const uint32_t cnt = sc.item_cnt[item], off = sc.item_off[item];
-    if (cnt == 0 || off == 0xFFFFFFFFu) continue;
+    const uint32_t cnt = sc.item_cnt[item];
+    const uint64_t off = sc.item_off[item];
+    if (cnt == 0 || off == ~0ull) continue;
     const uint64_t dst = out_off[sc.item_q[item]] + sc.item_pre[item];
     for (uint32_t i = lane; i < cnt; i += 32)
       if (dst + i < out_cap) out[dst + i] = sc.arena[off + i];
@@ -368,7 +369,7 @@ size_t query_batch_scratch_bytes(const bp_list *h_lists, uint32_t n_terms, const
     if (nmin == UINT64_MAX) continue;
     items += ((nmin + 127) / 128 + chunk - 1) / chunk;
   }
-  return q_layout(h_term_off[nq], nq, std::min<uint64_t>(out_cap, 0xFFFFFFF0ull), items).total + 4 * 256;
+  return q_layout(h_term_off[nq], nq, out_cap, items).total + 4 * 256;
 }
 
 int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_terms,
@@ -379,9 +380,9 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
   const Tuning tu = tuning();
   const uint32_t chunk = std::max<uint32_t>(1, std::min<uint32_t>(tu.query_chunk_blocks, kMaxChunk));
   const uint32_t warps = tu.query_warps == 4 ? 4 : 8;
-  const uint64_t arena_cap = std::min<uint64_t>(out_cap, 0xFFFFFFF0ull);
+  const uint64_t arena_cap = out_cap;
   const QLayout L = q_layout_fit(total_terms, nq, arena_cap, scratch_bytes);
-  if (scratch_bytes < L.total || L.max_items == 0) return BP_ERR_SCRATCH;
+  if (scratch_bytes < L.total) return BP_ERR_SCRATCH;
   const uint32_t max_items = (uint32_t)std::min<uint64_t>(L.max_items, 0xFFFFFFF0ull);
   const QScratch sc = q_carve(scratch, L);
   if (cudaMemsetAsync(sc.counters, 0, 256, s) != cudaSuccess) return BP_ERR_CUDA;
@@ -403,8 +404,8 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
   q_plan_kernel<<<(nq + 255) / 256, 256, 0, s>>>(lists, n_terms, terms, term_off, nq, sc, chunk,
                                                   status);
   scan_u32_kernel<<<1, 1024, 0, s>>>(sc.base, nq);
-  q_main_kernel<<<grid, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items,
-                                            (uint32_t)arena_cap, chunk,
+  q_main_kernel<<<grid, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items, arena_cap,
+                                            chunk,
                                             std::min<uint32_t>(tu.dense_blocks, kIxDenseMax),
                                             status);
   const int cgrid = (int)std::min<uint64_t>((nq + 7) / 8, 65535);

@@ -135,8 +135,11 @@ def test_capacity_and_bad_terms(small_index):
     terms = np.array([3, 3], np.uint32)
     toff = np.array([0, 1, 2], np.uint64)
     with pytest.raises(capi.BPError) as e:
-        idx.query_batch(terms, toff, out_cap=10)
+        idx.query_batch(terms, toff, out_cap=10, retry=False)
     assert e.value.code == capi.BP_ERR_CAPACITY
+    res = idx.query_batch(terms, toff, out_cap=10)  # sized exactly on the second call
+    assert idx.last_total == 2 * int(idx.h_lists["n"][3])
+    assert np.array_equal(res[0], vals[int(offs[3]):int(offs[4])])
     with pytest.raises(capi.BPError) as e:
         idx.query_batch(np.array([idx.n_terms + 5], np.uint32), np.array([0, 1], np.uint64),
                         out_cap=10)
@@ -152,11 +155,17 @@ def test_full_size_index_sampled(orc):
     vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
     idx = api.Index(vals, offs)
     terms, toff = W.queries(lens, 100_000, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
-    res = idx.query_batch(terms, toff, out_cap=1 << 29)
+    out, o, c = idx.query_batch(terms, toff, out_cap=1 << 30, on_device=True)
+    print("total answer values", idx.last_total)
+    assert int(o[-1]) == idx.last_total == int(c.astype(np.uint64).sum())
+
+    def answer(q):
+        return api.as_u32(out[int(o[q]):int(o[q]) + int(c[q])])
+
     rng = np.random.default_rng(1)
     for q in rng.choice(100_000, 300, replace=False):
         t = terms[int(toff[q]):int(toff[q + 1])]
-        assert np.array_equal(res[q], orc.svs(lists_of(vals, offs, t))), q
-    for q in range(0, 100_000, 97):
-        r = res[q]
-        assert np.all(np.diff(r.astype(np.int64)) > 0)
+        assert np.array_equal(answer(q), orc.svs(lists_of(vals, offs, t))), q
+    for q in range(0, 100_000, 997):
+        r = answer(q).astype(np.int64)
+        assert np.all(np.diff(r) > 0)
