@@ -227,7 +227,7 @@ int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a,
  * (16-byte aligned) and a device array d_lists of n_terms descriptors
  * (enc_offset, enc_bytes, n; the other fields are ignored).  A query is a
  * set of term ids; its answer is the sorted intersection of their lists
- * (Section 6, Set-vs-Set from the shortest list; P:196, 967 of the paper). */
+ * (Section 1 and Section 6: Set-vs-Set, from the shortest list). */
 
 /* Scratch needed by bp_query_batch; host copies of the index descriptors
  * and of the queries' terms, out_cap as passed to bp_query_batch. */
