@@ -222,6 +222,29 @@ int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a,
                       uint32_t *d_count, void *d_scratch, size_t scratch_bytes,
                       uint32_t *d_status, void *stream);
 
+/* The paper has no counterpart to this call; it exists for the library's
+ * users.  bp_intersect_pair for callers that cannot allocate device memory:
+ * a plug-in that only works on the buffers its host framework hands it, a
+ * server whose pool already holds all device memory, or latency-bound code
+ * that must not call cudaMalloc (it can synchronise the device) has no way
+ * to provide the scratch buffer bp_intersect_pair asks for.  This call does the
+ * same fused intersection of two BP_LAYOUT_GPU lists (arguments, output and
+ * errors as in bp_intersect_pair with BP_MODE_FUSED) but keeps its scratch
+ * in a 256 KiB array of device memory that the library reserves on every GPU
+ * that loads it, for the life of the process; it allocates nothing.  The
+ * shorter list may hold at most BP_NOALLOC_MAX_SHORT_LIST integers (larger:
+ * BP_ERR_SCRATCH, nothing enqueued).  The first call on a device looks up
+ * the array's device address (a runtime call), so make that first call
+ * before any stream capture.  All calls share the array and each clears the
+ * part it uses: calls whose work overlaps on the GPU corrupt each other's
+ * results, so issue them in order on one stream. */
+#define BP_NOALLOC_MAX_SHORT_LIST 33552384u
+int bp_intersect_pair_noalloc(const uint8_t *d_a, size_t a_bytes, size_t n_a,
+                              const uint8_t *d_b, size_t b_bytes, size_t n_b,
+                              uint32_t *d_out, size_t out_cap,
+                              uint32_t *d_count, uint32_t *d_status,
+                              void *stream);
+
 /* ---- conjunctive queries over a resident index -------------------------- *
  * The index is a device buffer d_data holding one GL stream per term
  * (16-byte aligned) and a device array d_lists of n_terms descriptors
