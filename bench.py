@@ -267,6 +267,174 @@ def time_launches(stream, fn, steps: int, warmup: int):
     return e0.elapsed_time(e1) / steps
 
 
+def gl_widths(enc: np.ndarray) -> np.ndarray:
+    """Bit widths of the blocks of a GL stream (from its header fields)."""
+    h = enc[:64].view(np.uint32)
+    nb, off_bw = int(h[3]), int(h[8])
+    return enc[off_bw:off_bw + nb]
+
+
+def pair_sweep(stream, reps: int):
+    """Longer list 2^22 uniform values of [0,2^26); shorter lists of 2^22 .. 2^8
+    values sharing 10% of theirs; fused vs unfused bp_intersect_pair, L2
+    flushed before every call (one pair fits in L2)."""
+    import torch
+    import workloads as W
+    from paper_1401_6399_gb300 import api, capi
+    GL = capi.BP_LAYOUT_GPU
+    f = W.uniform(1 << 22, 0, 1 << 26, 0x3000)
+    encf = capi.bp_encode(f, GL, nthreads=8)
+    ef = api.to_device(encf)
+    first = f[::128].astype(np.int64)
+    bw = gl_widths(encf).astype(np.int64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for m in (1 << 22, 1 << 18, 1 << 14, 1 << 10, 1 << 8):
+        k = round(0.1 * m)
+        r = W.pair_short(f, m, k, 1 << 26, 0x3000 + m)
+        encr = capi.bp_encode(r, GL, nthreads=8)
+        er = api.to_device(encr)
+        row = {}
+        answers = {}
+        for name, mode in (("fused", capi.BP_MODE_FUSED), ("unfused", capi.BP_MODE_UNFUSED)):
+            cap = m
+            res = torch.empty(cap, dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+            sb = capi.bp_intersect_scratch_bytes(m, f.size, GL, mode)
+            scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device="cuda")
+            st = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+            def call():
+                capi.check(capi.bp_intersect_pair(er.data_ptr(), er.numel(), m, ef.data_ptr(),
+                                                  ef.numel(), f.size, GL, mode, res.data_ptr(),
+                                                  cap, cnt.data_ptr(), scratch.data_ptr(), sb,
+                                                  st.data_ptr(), stream.cuda_stream), "pair")
+            with torch.cuda.stream(stream):
+                call()
+            stream.synchronize()
+            assert int(st.item()) == 0 and int(cnt.item()) == k
+            answers[name] = res[:k].clone()
+            tot = 0.0
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            row[name + "_us"] = round(1e3 * tot / reps, 2)
+        assert torch.equal(answers["fused"], answers["unfused"])
+        cand = np.unique(np.searchsorted(first, r.astype(np.int64), side="right") - 1)
+        cand = cand[cand >= 0]
+        alg = encr.size + 4 * first.size + int(16 * bw[cand].sum()) + 4 * k
+        row["speedup_fused"] = round(row["unfused_us"] / row["fused_us"], 2)
+        row["fused_alg_bytes"] = alg
+        row["fused_gbs"] = round(alg / (row["fused_us"] * 1e-6) / 1e9, 1)
+        row["candidate_blocks"] = int(cand.size)
+        out[f"m=2^{int(np.log2(m))}"] = row
+    return out
+
+
+def batched_queries(stream, reps: int, plain_queries: int):
+    """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
+    2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
+    100,000 queries of 2-5 terms drawn in proportion to list length.  One
+    autotuned, CUDA-graph-captured bp_query_batch vs bp_query_one per query."""
+    import torch
+    import workloads as W
+    from paper_1401_6399_gb300 import api, autotune, capi
+    t0 = time.time()
+    lens = W.zipf_lengths(1 << 19, 1_500_000_000, 1 << 24)
+    vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
+    idx = api.Index(vals, offs)
+    terms, toff = W.queries(lens, 100_000, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
+    setup_s = time.time() - t0
+    # autotune on a 5,000-query sample of the batch
+    sample_n = 5000
+    tuned = autotune.tune_queries(idx, terms[: int(toff[sample_n])], toff[: sample_n + 1],
+                                  reps=2)
+    # exact output size, then a graph-captured batch
+    _, o, _ = idx.query_batch(terms, toff, out_cap=1 << 30, on_device=True)
+    total = int(o[-1])
+    nq = toff.size - 1
+    dev = "cuda"
+    d_terms = torch.from_numpy(terms.view(np.int32).copy()).to(dev)
+    d_off = torch.from_numpy(toff.view(np.int64).copy()).to(dev)
+    out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    out_off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    counts = torch.empty(nq, dtype=torch.int32, device=dev)
+    sb = capi.bp_query_batch_scratch_bytes(idx.h_lists, terms, toff, total)
+    scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    with torch.cuda.stream(stream):
+        idx.query_batch_async(d_terms, d_off, nq, terms.size, out, out_off, counts, scratch, st,
+                              stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        idx.query_batch_async(d_terms, d_off, nq, terms.size, out, out_off, counts, scratch, st,
+                              torch.cuda.current_stream())
+    with torch.cuda.stream(stream):  # replays run on the current stream
+        g.replay()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    assert int(st.item()) == 0
+    o = out_off.cpu().numpy().view(np.uint64)
+    c = counts.cpu().numpy().view(np.uint32)
+    # plain per-query path on the first queries (decode every list, then
+    # intersect pairwise), launched back to back; same answers required
+    qn = min(plain_queries, nq)
+    lens_np = idx.h_lists["n"].astype(np.int64)
+    qterms = [terms[int(toff[q]):int(toff[q + 1])] for q in range(qn)]
+    caps = np.array([max(1, int(lens_np[t].min())) for t in qterms], np.int64)
+    pos = np.concatenate([[0], np.cumsum(caps)])
+    pout = torch.empty(int(pos[-1]), dtype=torch.int32, device=dev)
+    pcnt = torch.zeros(qn, dtype=torch.int32, device=dev)
+    psb = max(capi.bp_query_one_scratch_bytes(idx.h_lists, t) for t in qterms)
+    pscr = torch.empty(psb, dtype=torch.uint8, device=dev)
+    pst = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def plain_all():
+        for q in range(qn):
+            capi.check(capi.bp_query_one(idx.data.data_ptr(), idx.h_lists, qterms[q],
+                                         pout.data_ptr() + 4 * int(pos[q]), int(caps[q]),
+                                         pcnt.data_ptr() + 4 * q, pscr.data_ptr(), psb,
+                                         pst.data_ptr(), stream.cuda_stream), "bp_query_one")
+    plain_all()  # warm-up
+    stream.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    plain_all()
+    p1.record(stream)
+    p1.synchronize()
+    ms_plain = p0.elapsed_time(p1)
+    assert int(pst.item()) == 0
+    pc = pcnt.cpu().numpy()
+    for q in range(qn):
+        got = out[int(o[q]):int(o[q]) + int(c[q])]
+        want = pout[int(pos[q]):int(pos[q]) + int(pc[q])]
+        assert torch.equal(got, want), f"batched and plain answers differ for query {q}"
+    qps = nq / (ms * 1e-3)
+    qps_plain = qn / (ms_plain * 1e-3)
+    return {"queries": nq, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
+            "plain_queries_timed": qn, "plain_queries_per_s": round(qps_plain, 1),
+            "speedup_vs_plain": round(qps / qps_plain, 1), "answer_values": total,
+            "index_postings": int(lens.sum()), "index_bytes": idx.compressed_bytes,
+            "bits_per_posting": round(8 * idx.compressed_bytes / int(lens.sum()), 3),
+            "tuned": tuned["best"], "setup_s": round(setup_s, 1)}
+
+
 def run_ours(args, rank, world, local):
     import torch
     dist = dist_init(world, local)
@@ -393,6 +561,18 @@ def run_ours(args, rank, world, local):
             "gints": round(total_n / (ms_p * 1e-3) / 1e9, 2), "ms": round(ms_p, 4),
             "bits_per_int": round(8 * pbatch.compressed_bytes / total_n, 3)}
         del pbatch
+        del out
+        torch.cuda.empty_cache()
+        try:
+            extra["pair_sweep"] = pair_sweep(stream, reps=20)
+        except Exception as e:  # report, do not hide the headline
+            extra["pair_sweep"] = {"error": repr(e)[:300]}
+        try:
+            extra["batched_queries"] = batched_queries(stream, reps=5, plain_queries=2000)
+        except Exception as e:
+            extra["batched_queries"] = {"error": repr(e)[:300]}
+        torch.cuda.empty_cache()
+        out = torch.empty(total_n, dtype=torch.int32, device="cuda")
     clocks.stop()
     if extra:
         result["secondary"] = extra

@@ -18,10 +18,24 @@
 
 namespace bp {
 
-// The four deltas of `lane` from a block of width B at w (4B words).
-template <int B>
-__device__ __forceinline__ void gl_lane_deltas(const uint32_t *__restrict__ w, int lane,
-                                               uint32_t d[4]) {
+// Word sources for the unpacker: the block's 4b words in global memory
+// (read-only path) or already staged in shared memory.
+struct GlobalWords {
+  const uint32_t *w;
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return __ldg(w + i); }
+};
+struct SharedWords {
+  uint32_t base;  // shared-window address of word 0
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(base + 4u * i));
+    return v;
+  }
+};
+
+// The four deltas of `lane` from a block of width B (4B words from `ld`).
+template <int B, class L>
+__device__ __forceinline__ void gl_lane_deltas(const L &ld, int lane, uint32_t d[4]) {
   if constexpr (B == 0) {
     d[0] = d[1] = d[2] = d[3] = 0u;
   } else {
@@ -33,7 +47,7 @@ __device__ __forceinline__ void gl_lane_deltas(const uint32_t *__restrict__ w, i
     const uint32_t w0 = p >> 5, o = p & 31u;
     uint32_t a[NW + 1];
 #pragma unroll
-    for (int k = 0; k < NW; k++) a[k] = (w0 + k < 4u * B) ? __ldg(w + w0 + k) : 0u;
+    for (int k = 0; k < NW; k++) a[k] = (w0 + k < 4u * B) ? ld(w0 + k) : 0u;
     a[NW] = 0u;
     uint32_t u[UW + 1];
 #pragma unroll
@@ -49,11 +63,10 @@ __device__ __forceinline__ void gl_lane_deltas(const uint32_t *__restrict__ w, i
 }
 
 // Decoded values of `lane`: x[j] is block position 16c + 4j + s.
-template <int B>
-__device__ __forceinline__ void gl_lane_values(const uint32_t *__restrict__ w, uint32_t F,
-                                               int lane, uint32_t x[4]) {
+template <int B, class L>
+__device__ __forceinline__ void gl_lane_values(const L &ld, uint32_t F, int lane, uint32_t x[4]) {
   uint32_t d[4];
-  gl_lane_deltas<B>(w, lane, d);
+  gl_lane_deltas<B>(ld, lane, d);
   x[0] = d[0];
   x[1] = x[0] + d[1];
   x[2] = x[1] + d[2];
@@ -71,12 +84,13 @@ __device__ __forceinline__ void gl_lane_values(const uint32_t *__restrict__ w, u
 }
 
 // Runtime-width dispatch (b is warp-uniform, so the switch never diverges).
-__device__ __forceinline__ void gl_block_values(int b, const uint32_t *__restrict__ w,
-                                                uint32_t F, int lane, uint32_t x[4]) {
+template <class L>
+__device__ __forceinline__ void gl_block_values_from(int b, const L &ld, uint32_t F, int lane,
+                                                     uint32_t x[4]) {
   switch (b) {
 #define BP_CASE(B) \
   case B:          \
-    gl_lane_values<B>(w, F, lane, x); \
+    gl_lane_values<B>(ld, F, lane, x); \
     break;
     BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
     BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
@@ -87,6 +101,11 @@ __device__ __forceinline__ void gl_block_values(int b, const uint32_t *__restric
     default:
       x[0] = x[1] = x[2] = x[3] = 0u;
   }
+}
+
+__device__ __forceinline__ void gl_block_values(int b, const uint32_t *__restrict__ w,
+                                                uint32_t F, int lane, uint32_t x[4]) {
+  gl_block_values_from(b, GlobalWords{w}, F, lane, x);
 }
 
 // In-block position of x[j] for `lane`.
