@@ -27,8 +27,11 @@ struct PairArgs {
   uint32_t nf;
 };
 
+// vpw: values of the shorter list per warp (8..128, a power of two).  Warps
+// that share an r block each decode it and take their slice.
 __global__ void __launch_bounds__(kIxThreads)
-    fused_pair_kernel(PairArgs a, Compaction cp, TileOut to, uint32_t ntiles, uint32_t dense_max) {
+    fused_pair_kernel(PairArgs a, Compaction cp, TileOut to, uint32_t ntiles, uint32_t dense_max,
+                      uint32_t vpw) {
   __shared__ uint32_t s_r[kIxWarps][128];
   __shared__ uint32_t s_f[kIxWarps][kIxDenseMax * 128];
   __shared__ uint32_t s_wcnt[kIxWarps], s_base[1], s_tile;
@@ -44,17 +47,20 @@ __global__ void __launch_bounds__(kIxThreads)
 
   uint32_t v[4] = {0, 0, 0, 0};
   bool valid[4] = {false, false, false, false}, hit[4] = {false, false, false, false};
-  const uint32_t kb = t * kIxWarps + w;
-  if (okR && okF && kb < R.nblocks) {
+  const uint64_t p0 = ((uint64_t)t * kIxWarps + w) * vpw;  // first r position of this warp
+  if (okR && okF && p0 < a.nr) {
+    const uint32_t kb = (uint32_t)(p0 >> 7), s0 = (uint32_t)(p0 & 127u);
     const uint32_t cnt = gl_block_into(R, kb, s_r[w], lane, to.status);
     __syncwarp();
+    const uint32_t end = min(cnt, s0 + vpw);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      valid[k] = (uint32_t)(32 * k + lane) < cnt;
-      v[k] = valid[k] ? s_r[w][32 * k + lane] : 0u;
+      const uint32_t pos = s0 + 32u * k + lane;
+      valid[k] = pos < end;
+      v[k] = valid[k] ? s_r[w][pos] : 0u;
     }
-    if (cnt > 0)
-      gl_membership(F, v, valid, hit, s_r[w][0], s_r[w][cnt - 1], s_f[w], lane, dense_max,
+    if (end > s0)
+      gl_membership(F, v, valid, hit, s_r[w][s0], s_r[w][end - 1], s_f[w], lane, dense_max,
                     to.status);
   }
   tile_emit(v, hit, t, t == ntiles - 1, cp, to, s_wcnt, s_base);
@@ -87,16 +93,28 @@ __global__ void __launch_bounds__(kIxThreads)
 
 inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-uint32_t pair_tiles(uint64_t nr) {
-  const uint64_t chunks = (nr + 127) / 128;
+uint32_t pair_tiles(uint64_t nr, uint32_t vpw = 128) {
+  const uint64_t chunks = (nr + vpw - 1) / vpw;
   return (uint32_t)std::max<uint64_t>(1, (chunks + kIxWarps - 1) / kIxWarps);
+}
+
+// Values of the shorter list per warp: 128, unless the lists are so skewed
+// that every value probes a block of its own (ratio >= 128) and there are
+// too few values to fill the GPU -- then down to 8 (more warps, fewer
+// probes each).
+uint32_t pair_vpw(uint64_t nr, uint64_t nf) {
+  if (nr == 0 || nf < 128 * nr) return 128;
+  const uint64_t want_warps = 16ull * device_sm_count() * 8;
+  uint32_t vpw = 128;
+  while (vpw > 8 && (nr + vpw - 1) / vpw < want_warps) vpw >>= 1;
+  return vpw;
 }
 
 }  // namespace
 
 size_t intersect_scratch_bytes(size_t na, size_t nb, int layout, int mode) {
   const size_t nr = std::min(na, nb), nf = std::max(na, nb);
-  const size_t comp = up256(compaction_bytes(pair_tiles(nr)));
+  const size_t comp = up256(compaction_bytes(pair_tiles(nr, 8)));
   if (mode == BP_MODE_FUSED) return comp;
   size_t dec = 0;
   if (layout == BP_LAYOUT_PAPER) dec = up256(pl_scratch_bytes(bp_fmt::units_of(nf, 0), 1));
@@ -115,19 +133,22 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
   a.f_enc = swap ? da : db;
   a.f_bytes = swap ? a_bytes : b_bytes;
   a.nf = (uint32_t)(swap ? na : nb);
-  const uint32_t ntiles = pair_tiles(a.nr);
   uint8_t *sp = static_cast<uint8_t *>(scratch);
   const Compaction cp = compaction_at(sp);
-  if (cudaMemsetAsync(sp, 0, compaction_bytes(ntiles), s) != cudaSuccess) return BP_ERR_CUDA;
   TileOut to{out, out_cap, count, status};
   const Tuning &tu = tuning();
   if (mode == BP_MODE_FUSED) {
-    fused_pair_kernel<<<ntiles, kIxThreads, 0, s>>>(a, cp, to, ntiles,
-                                                    std::min<uint32_t>(tu.dense_blocks, kIxDenseMax));
+    const uint32_t vpw = pair_vpw(a.nr, a.nf);
+    const uint32_t ft = pair_tiles(a.nr, vpw);
+    if (cudaMemsetAsync(sp, 0, compaction_bytes(ft), s) != cudaSuccess) return BP_ERR_CUDA;
+    fused_pair_kernel<<<ft, kIxThreads, 0, s>>>(
+        a, cp, to, ft, std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw);
     return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
   }
   // unfused: decode both lists into scratch, then intersect the arrays
-  size_t off = up256(compaction_bytes(ntiles));
+  const uint32_t ntiles = pair_tiles(a.nr);
+  if (cudaMemsetAsync(sp, 0, compaction_bytes(ntiles), s) != cudaSuccess) return BP_ERR_CUDA;
+  size_t off = up256(compaction_bytes(pair_tiles(a.nr, 8)));
   uint32_t *dr = reinterpret_cast<uint32_t *>(sp + off);
   off += up256(4ull * a.nr + 16);
   uint32_t *df = reinterpret_cast<uint32_t *>(sp + off);

@@ -105,6 +105,104 @@ __device__ __forceinline__ uint32_t gl_block_into(const GlView &v, uint32_t k, u
   return min(128u, v.n - 128u * k);
 }
 
+// Payload word offset of block k of GL list v (the superblock's offset plus
+// 4x the widths of the blocks before k in it), computed by one lane.
+__device__ __forceinline__ uint32_t gl_block_woff(const GlView &v, uint32_t k) {
+  const uint32_t q = k >> 5, j = k & 31u;
+  const uint4 *w4 = reinterpret_cast<const uint4 *>(v.bw + 32u * q);
+  const uint4 a = __ldg(w4), b = (j > 16u) ? __ldg(w4 + 1) : make_uint4(0, 0, 0, 0);
+  const uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const uint32_t lo = 4u * i;  // bytes lo..lo+3 of the 32 widths
+    const uint32_t keep = j >= lo + 4u ? 0xFFFFFFFFu : (j <= lo ? 0u : (0xFFFFFFFFu >> (8u * (4u - (j - lo)))));
+    sum = __dp4a(wd[i] & keep, 0x01010101u, sum);
+  }
+  return __ldg(v.sbo + q) + 4u * sum;
+}
+
+// Is p in block k of GL list v?  Four lanes (column s = lane & 3 each) decode
+// their column of the block -- the contiguous bit string [32bs, 32b(s+1)),
+// a running sum from the block's first value -- and stop as soon as the
+// increasing column reaches p.  Returns the lookup's answer in all 4 lanes.
+__device__ __forceinline__ bool column_lookup(const GlView &v, uint32_t k, uint32_t p,
+                                              bool active, int lane, uint32_t *status) {
+  const uint32_t s = lane & 3u;
+  bool found = false;
+  if (active) {
+    const uint32_t b = v.bw[k];
+    const uint32_t woff = gl_block_woff(v, k);
+    if (b > 32u || woff + 4u * b > v.pw) {
+      set_status(status, BP_ERR_CORRUPT);
+    } else {
+      const uint32_t F = __ldg(v.first + k);
+      const uint32_t cnt = min(128u, v.n - 128u * k);
+      const uint32_t *w = v.payload + woff + b * s;
+      const uint32_t nw = b;  // words of this column
+      uint32_t wi = 0;
+      uint32_t lo = nw > 0 ? __ldg(w) : 0u, hi = nw > 1 ? __ldg(w + 1) : 0u;
+      uint32_t nx = nw > 2 ? __ldg(w + 2) : 0u;
+      const uint32_t mask = b >= 32u ? 0xFFFFFFFFu : ((1u << b) - 1u);
+      uint32_t off = 0, x = F;
+      for (uint32_t t = 0; t < 32u; t++) {
+        x += __funnelshift_r(lo, hi, off) & mask;
+        if (4u * t + s >= cnt) break;  // past the block's last value
+        if (x >= p) {
+          found = (x == p);
+          break;
+        }
+        off += b;
+        if (off >= 32u) {
+          off -= 32u;
+          lo = hi;
+          hi = nx;
+          wi++;
+          nx = (wi + 2u < nw) ? __ldg(w + wi + 2u) : 0u;
+        }
+      }
+    }
+  }
+  const uint32_t grp = 0xFu << (lane & ~3);
+  return (__ballot_sync(kFull, found) & grp) != 0;
+}
+
+// Resolve the probes of a warp (lane holds positions 32k + lane; cb[k] its
+// candidate block, < klo when there is none) eight at a time: probe i of a
+// round goes to lanes 4i..4i+3.
+__device__ __forceinline__ void lookup_probes(const GlView &f, const uint32_t v[4],
+                                              const bool valid[4], const int64_t cb[4],
+                                              int64_t klo, bool hit[4], int lane,
+                                              uint32_t *status) {
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    hit[k] = false;
+    const bool want = valid[k] && cb[k] >= klo;
+    uint32_t pend = __ballot_sync(kFull, want);  // probes of this register
+    while (pend) {                                // up to 8 per round
+      // the i-th set bit of pend goes to lane group i
+      const int g = lane >> 2;
+      uint32_t m = pend;
+      for (int i = 0; i < g && m; i++) m &= m - 1;
+      const bool act = m != 0;
+      const int src = act ? __ffs(m) - 1 : 0;
+      const uint32_t pv = __shfl_sync(kFull, v[k], src);
+      const uint32_t pb = (uint32_t)__shfl_sync(kFull, (uint32_t)cb[k], src);
+      const bool found = column_lookup(f, pb, pv, act, lane, status);
+      // hand each answer back to the lane that owns the probe
+      const uint32_t ans = __ballot_sync(kFull, act && (lane & 3) == 0 && found);
+      // lane L owns probe number r = popc(pend & lanemask_lt(L)) of this round
+      const uint32_t mine = pend & (1u << lane);
+      if (mine) {
+        const uint32_t r = __popc(pend & ((1u << lane) - 1u));
+        if (r < 8u) hit[k] = (ans >> (4u * r)) & 1u;
+      }
+      // drop the (up to 8) probes handled this round
+      for (int i = 0; i < 8 && pend; i++) pend &= pend - 1;
+    }
+  }
+}
+
 // Membership of the warp's values (lane holds positions 32k + lane, k < 4,
 // valid where valid[k]) in GL list f.  smem: kIxDenseMax*128 words of this
 // warp.  dense_max: span threshold of the dense regime.
@@ -132,31 +230,11 @@ __device__ __forceinline__ void gl_membership(const GlView &f, const uint32_t v[
     __syncwarp();
     return;
   }
+  // sparse regime: every value looks up its own candidate block
   int64_t cb[4];
-  bool pend[4];
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
-    cb[k] = valid[k] ? lane_ubound(f.first, klo, khi, v[k]) : klo - 1;
-    pend[k] = valid[k] && cb[k] >= klo;
-  }
-  for (;;) {
-    int64_t blk = -1;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t m = __ballot_sync(kFull, pend[k]);
-      if (blk < 0 && m) blk = __shfl_sync(kFull, cb[k], __ffs(m) - 1);
-    }
-    if (blk < 0) break;
-    const uint32_t c = gl_block_into(f, (uint32_t)blk, smem, lane, status);
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-      if (pend[k] && cb[k] == blk) {
-        hit[k] = smem_contains(smem, c, v[k]);
-        pend[k] = false;
-      }
-    __syncwarp();
-  }
+  for (int k = 0; k < 4; k++) cb[k] = valid[k] ? lane_ubound(f.first, klo, khi, v[k]) : klo - 1;
+  lookup_probes(f, v, valid, cb, klo, hit, lane, status);
 }
 
 // Same for a decoded, sorted f in global memory.
