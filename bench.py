@@ -427,12 +427,48 @@ def batched_queries(stream, reps: int, plain_queries: int):
         assert torch.equal(got, want), f"batched and plain answers differ for query {q}"
     qps = nq / (ms * 1e-3)
     qps_plain = qn / (ms_plain * 1e-3)
+    batched_queries.index = (idx, lens)  # reused by the serving measurement
     return {"queries": nq, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
             "plain_queries_timed": qn, "plain_queries_per_s": round(qps_plain, 1),
             "speedup_vs_plain": round(qps / qps_plain, 1), "answer_values": total,
             "index_postings": int(lens.sum()), "index_bytes": idx.compressed_bytes,
             "bits_per_posting": round(8 * idx.compressed_bytes / int(lens.sum()), 3),
             "tuned": tuned["best"], "setup_s": round(setup_s, 1)}
+
+
+def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
+    """Open-loop Poisson arrivals of 2-8-term queries against the resident
+    index; the engine batches continuously over 4 slots of 1 GiB (at most
+    4 GiB of scratch and answers in flight).  Latency = completion - arrival."""
+    import workloads as W
+    from paper_1401_6399_gb300 import api
+    out = {}
+    srv = api.Server(idx, slots=4, max_batch_queries=8192, max_terms=8, slot_bytes=1 << 30,
+                     deliver_answers=False)
+    try:
+        for rate in rates:
+            n = int(min(300_000, rate * 5))
+            terms, toff = W.queries(lens, n, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5000 + int(rate))
+            arrivals = W.poisson_arrivals(rate, n, 0x5100 + int(rate))
+            tags = np.arange(n, dtype=np.uint64)
+            srv.replay(tags, terms, toff, arrivals)
+            srv.drain(600.0)
+            res = srv.poll(with_answers=False)
+            assert len(res) == n and all(r[2] == 0 for r in res)
+            sub = np.array([r[3] for r in res])
+            done = np.array([r[4] for r in res])
+            lat_ms = (done - sub) * 1e3
+            span = done.max() - sub.min()
+            out[f"{int(rate)}/s"] = {
+                "queries": n, "offered_qps": rate, "achieved_qps": round(n / span, 1),
+                "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                "p999_ms": round(float(np.percentile(lat_ms, 99.9)), 3),
+                "answer_values": int(sum(r[1] for r in res))}
+        out["engine"] = srv.stats()
+    finally:
+        srv.close()
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -571,6 +607,12 @@ def run_ours(args, rank, world, local):
             extra["batched_queries"] = batched_queries(stream, reps=5, plain_queries=2000)
         except Exception as e:
             extra["batched_queries"] = {"error": repr(e)[:300]}
+        try:
+            if hasattr(batched_queries, "index"):
+                extra["serving"] = serving(*batched_queries.index)
+                del batched_queries.index
+        except Exception as e:
+            extra["serving"] = {"error": repr(e)[:300]}
         torch.cuda.empty_cache()
         out = torch.empty(total_n, dtype=torch.int32, device="cuda")
     clocks.stop()

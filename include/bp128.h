@@ -292,6 +292,74 @@ int bp_query_one(const uint8_t *d_data, const bp_list *h_lists,
                  void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
                  void *stream);
 
+/* ---- serving ------------------------------------------------------------- *
+ * A serving engine over a resident index (not in the paper: its query
+ * processing of Section 7.6, run continuously).  Queries are submitted from
+ * any host thread; a dispatcher thread batches them continuously: whenever
+ * one of `slots` batch slots is free it admits waiting queries in arrival
+ * order as long as their scratch and answer capacity fit the slot's memory,
+ * and launches them with bp_query_batch on the slot's stream, so new
+ * requests join while earlier batches are still on the GPU and several
+ * batches overlap on the device.  Answers are written by the kernels into
+ * the slot's pinned host memory, which must be device-accessible (pinned
+ * memory on a unified-address system).  The engine allocates no device or
+ * pinned memory and creates only one event per slot. */
+typedef struct bp_server bp_server;
+
+typedef struct bp_server_config {
+  uint32_t slots;             /* batches in flight (one stream each), 1..16 */
+  uint32_t max_batch_queries; /* queries per batch                         */
+  uint32_t max_terms;         /* terms per query, 1..64                    */
+  uint32_t deliver_answers;   /* 1: bp_server_poll returns answer arrays    */
+  uint64_t slot_bytes;        /* device bytes per slot (scratch + answers)  */
+  uint64_t reserved[4];
+} bp_server_config;
+
+typedef struct bp_server_result {
+  uint64_t tag;
+  uint32_t count;          /* answer values                               */
+  int32_t status;          /* BP_OK, or the error of the query's batch    */
+  double submit_s, done_s; /* steady-clock seconds: submission, completion */
+  const uint32_t *answer;  /* deliver_answers = 1: valid until the next poll */
+} bp_server_result;
+
+/* Device bytes (slots x slot_bytes) and pinned host bytes the engine needs. */
+size_t bp_server_device_bytes(const bp_server_config *cfg);
+size_t bp_server_host_bytes(const bp_server_config *cfg);
+
+/* Start an engine.  d_data/d_lists: the index (as bp_query_batch); h_lists:
+ * host copy of the descriptors; d_mem, h_pinned: caller buffers of the sizes
+ * above; streams: cfg->slots CUDA streams.  NULL on error (*err set). */
+bp_server *bp_server_create(const uint8_t *d_data, const bp_list *d_lists,
+                            const bp_list *h_lists, uint32_t n_terms,
+                            const bp_server_config *cfg, void *d_mem,
+                            void *h_pinned, void *const *streams, int *err);
+
+/* Queue one query of k terms under `tag` (thread-safe). */
+int bp_server_submit(bp_server *s, uint64_t tag, const uint32_t *terms,
+                     uint32_t k);
+
+/* Open-loop load: submit query i (terms[term_off[i]..term_off[i+1])) at
+ * arrival_s[i] seconds after the call starts, on the calling thread,
+ * whatever the engine's progress. */
+int bp_server_replay(bp_server *s, const uint64_t *tags, const uint32_t *terms,
+                     const uint64_t *term_off, uint32_t n,
+                     const double *arrival_s);
+
+/* Move up to max finished queries to out; returns how many. */
+uint32_t bp_server_poll(bp_server *s, bp_server_result *out, uint32_t max);
+
+/* Wait until every submitted query has finished (BP_ERR_TIMEOUT after
+ * timeout_s); returns the first error seen, else BP_OK. */
+int bp_server_drain(bp_server *s, double timeout_s);
+
+/* out = {submitted, completed, batches launched, rejected (too large for a
+ * slot), most slots busy at once, queries waiting}. */
+int bp_server_stats(bp_server *s, uint64_t out[6]);
+
+/* Finish the queued and running queries, then stop the engine. */
+void bp_server_destroy(bp_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -233,3 +233,81 @@ class Index:
                                 _stream(stream)), "bp_query_one")
         check_status(st, "bp_query_one")
         return out[: int(cnt.item())]
+
+
+class Server:
+    """The serving engine (bp_server_*) over a resident Index: PyTorch
+    allocates its device memory, pinned host memory and streams."""
+
+    def __init__(self, index: Index, slots: int = 4, max_batch_queries: int = 4096,
+                 max_terms: int = 8, slot_bytes: int = 1 << 30, deliver_answers: bool = True):
+        import ctypes as C
+        self.index = index
+        self.cfg = capi.bp_server_config(slots, max_batch_queries, max_terms,
+                                         1 if deliver_answers else 0, slot_bytes)
+        self.d_mem = torch.empty(capi.lib.bp_server_device_bytes(C.byref(self.cfg)),
+                                 dtype=torch.uint8, device=index.device)
+        self.h_mem = torch.empty(capi.lib.bp_server_host_bytes(C.byref(self.cfg)),
+                                 dtype=torch.uint8).pin_memory()
+        self.streams = [torch.cuda.Stream(device=index.device) for _ in range(slots)]
+        sp = (C.c_void_p * slots)(*[s.cuda_stream for s in self.streams])
+        err = C.c_int(0)
+        self.h_lists = np.ascontiguousarray(index.h_lists)
+        self.ptr = capi.lib.bp_server_create(
+            index.data.data_ptr(), index.d_lists.data_ptr(), self.h_lists.ctypes.data,
+            index.n_terms, C.byref(self.cfg), self.d_mem.data_ptr(), self.h_mem.data_ptr(), sp,
+            C.byref(err))
+        if not self.ptr:
+            raise capi.BPError(err.value, "bp_server_create")
+        self._res = (capi.bp_server_result * 65536)()
+
+    def submit(self, tag: int, terms) -> None:
+        t = np.ascontiguousarray(terms, np.uint32)
+        check(capi.lib.bp_server_submit(self.ptr, tag, t.ctypes.data if t.size else None,
+                                        t.size), "bp_server_submit")
+
+    def replay(self, tags, terms, term_off, arrival_s) -> None:
+        tags = np.ascontiguousarray(tags, np.uint64)
+        terms = np.ascontiguousarray(terms, np.uint32)
+        term_off = np.ascontiguousarray(term_off, np.uint64)
+        arrival_s = np.ascontiguousarray(arrival_s, np.float64)
+        check(capi.lib.bp_server_replay(self.ptr, tags.ctypes.data, terms.ctypes.data,
+                                        term_off.ctypes.data, tags.size,
+                                        arrival_s.ctypes.data), "bp_server_replay")
+
+    def poll(self, with_answers: bool = True) -> list:
+        out = []
+        while True:
+            n = capi.lib.bp_server_poll(self.ptr, self._res, len(self._res))
+            for i in range(n):
+                r = self._res[i]
+                ans = None
+                if with_answers and r.answer:
+                    ans = np.ctypeslib.as_array(r.answer, shape=(r.count,)).copy()
+                elif with_answers and r.status == capi.BP_OK:
+                    ans = np.zeros(0, np.uint32)
+                out.append((int(r.tag), int(r.count), int(r.status), float(r.submit_s),
+                            float(r.done_s), ans))
+            if n < len(self._res):
+                return out
+
+    def drain(self, timeout_s: float = 120.0) -> None:
+        check(capi.lib.bp_server_drain(self.ptr, timeout_s), "bp_server_drain")
+
+    def stats(self) -> dict:
+        import ctypes as C
+        a = (C.c_uint64 * 6)()
+        check(capi.lib.bp_server_stats(self.ptr, a), "bp_server_stats")
+        keys = ("submitted", "completed", "batches", "rejected", "max_busy_slots", "waiting")
+        return dict(zip(keys, [int(x) for x in a]))
+
+    def close(self) -> None:
+        if self.ptr:
+            capi.lib.bp_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -23,6 +23,18 @@ class bp_tuning(C.Structure):
     _fields_ = [("dense_blocks", C.c_uint32), ("query_chunk_blocks", C.c_uint32),
                 ("query_warps", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
+class bp_server_config(C.Structure):
+    _fields_ = [("slots", C.c_uint32), ("max_batch_queries", C.c_uint32),
+                ("max_terms", C.c_uint32), ("deliver_answers", C.c_uint32),
+                ("slot_bytes", C.c_uint64), ("reserved", C.c_uint64 * 4)]
+
+
+class bp_server_result(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("count", C.c_uint32), ("status", C.c_int32),
+                ("submit_s", C.c_double), ("done_s", C.c_double),
+                ("answer", C.POINTER(C.c_uint32))]
+
+
 # struct bp_list (48 bytes)
 BP_LIST = np.dtype([("enc_offset", "<u8"), ("enc_bytes", "<u8"), ("out_offset", "<u8"),
                     ("unit_base", "<u8"), ("n", "<u4"), ("layout", "<u4"),
@@ -63,6 +75,16 @@ _decl("bp_query_batch", _int, _vp, _vp, _u32, _vp, _vp, _u64, _u32, _vp, _u64, _
       _sz, _vp, _vp)
 _decl("bp_query_one_scratch_bytes", _sz, _vp, _u32, _vp, _u32)
 _decl("bp_query_one", _int, _vp, _vp, _u32, _vp, _u32, _vp, _sz, _vp, _vp, _sz, _vp, _vp)
+_decl("bp_server_device_bytes", _sz, C.POINTER(bp_server_config))
+_decl("bp_server_host_bytes", _sz, C.POINTER(bp_server_config))
+_decl("bp_server_create", _vp, _vp, _vp, _vp, _u32, C.POINTER(bp_server_config), _vp, _vp,
+      C.POINTER(_vp), C.POINTER(_int))
+_decl("bp_server_submit", _int, _vp, _u64, _vp, _u32)
+_decl("bp_server_replay", _int, _vp, _vp, _vp, _vp, _u32, _vp)
+_decl("bp_server_poll", _u32, _vp, C.POINTER(bp_server_result), _u32)
+_decl("bp_server_drain", _int, _vp, C.c_double)
+_decl("bp_server_stats", _int, _vp, C.POINTER(C.c_uint64))
+_decl("bp_server_destroy", None, _vp)
 _decl("bp_get_tuning", _int, C.POINTER(bp_tuning))
 _decl("bp_set_tuning", _int, C.POINTER(bp_tuning))
 _decl("bp_intersect_scratch_bytes", _sz, _sz, _sz, _int, _int)

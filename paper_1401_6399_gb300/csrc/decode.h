@@ -70,6 +70,11 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
                        uint32_t nq, uint32_t *out, uint64_t out_cap, uint64_t *out_off,
                        uint32_t *counts, void *scratch, size_t scratch_bytes, uint32_t *status,
                        cudaStream_t s);
+// Work items of a query whose shortest list has nmin integers, and the
+// scratch of a batch from its totals (incremental forms of the above).
+uint64_t query_items(uint64_t nmin);
+size_t query_batch_scratch_for(uint64_t total_terms, uint32_t nq, uint64_t out_cap,
+                               uint64_t items);
 size_t query_one_scratch_bytes(const bp_list *h_lists, const uint32_t *h_terms, uint32_t k);
 int launch_query_one(const uint8_t *data, const bp_list *h_lists, const uint32_t *h_terms,
                      uint32_t k, uint32_t *out, uint64_t out_cap, uint32_t *count, void *scratch,

@@ -357,6 +357,17 @@ int g_main_smem_set = 0;
 
 // ---- host side -----------------------------------------------------------------------------------
 
+uint64_t query_items(uint64_t nmin) {
+  const uint32_t chunk = std::max<uint32_t>(1, std::min<uint32_t>(tuning().query_chunk_blocks,
+                                                                 kMaxChunk));
+  return ((nmin + 127) / 128 + chunk - 1) / chunk;
+}
+
+size_t query_batch_scratch_for(uint64_t total_terms, uint32_t nq, uint64_t out_cap,
+                               uint64_t items) {
+  return q_layout(total_terms, nq, out_cap, items).total + 4 * 256;
+}
+
 size_t query_batch_scratch_bytes(const bp_list *h_lists, uint32_t n_terms, const uint32_t *h_terms,
                                  const uint64_t *h_term_off, uint32_t nq, uint64_t out_cap) {
   const uint32_t chunk = std::max<uint32_t>(1, std::min<uint32_t>(tuning().query_chunk_blocks,

@@ -1,0 +1,80 @@
+"""The serving engine: continuous batching of conjunctive queries over a
+resident index.  Every answer must be the same when its query runs alone and
+when it runs in an open-loop mix with others (and equal to the oracle's
+Set-vs-Set), batches must overlap on the device, and queries too large for a
+slot must be rejected without disturbing the others."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1401_6399_gb300.build import build  # noqa: E402
+
+build()
+from paper_1401_6399_gb300 import api, capi  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def index():
+    lens = W.zipf_lengths(1 << 13, 20_000_000, 1 << 20)
+    vals, offs = W.many("clustered", lens, 0, 1 << 22, 0x4100)
+    return api.Index(vals, offs), vals, offs
+
+
+def svs(orc, vals, offs, terms):
+    return orc.svs([vals[int(offs[t]):int(offs[t + 1])] for t in terms])
+
+
+def test_alone_equals_mixed_equals_oracle(orc, index):
+    idx, vals, offs = index
+    terms, toff = W.queries(np.diff(offs), 400, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5001)
+    n = toff.size - 1
+    srv = api.Server(idx, slots=4, max_batch_queries=64, max_terms=8, slot_bytes=256 << 20)
+    try:
+        alone = {}
+        for q in range(n):  # one query at a time
+            srv.submit(q, terms[int(toff[q]):int(toff[q + 1])])
+            srv.drain()
+            (tag, cnt, st, t0, t1, ans), = srv.poll()
+            assert tag == q and st == capi.BP_OK and ans.size == cnt
+            alone[q] = ans
+        # the same queries in an open-loop mix at 200,000 queries/s
+        arrivals = W.poisson_arrivals(200_000.0, n, 0x5002)
+        srv.replay(np.arange(n) + 1000, terms, toff, arrivals)
+        srv.drain()
+        mixed = {tag - 1000: ans for (tag, cnt, st, t0, t1, ans) in srv.poll()}
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert sorted(mixed) == list(range(n))
+    for q in range(n):
+        want = svs(orc, vals, offs, terms[int(toff[q]):int(toff[q + 1])])
+        assert np.array_equal(alone[q], want), q
+        assert np.array_equal(mixed[q], want), q
+    assert st["completed"] == st["submitted"] == 2 * n
+    assert st["batches"] > n  # alone: one batch each; mixed: several batches
+    assert st["max_busy_slots"] >= 2  # batches overlapped on the device
+
+
+def test_oversized_query_is_rejected_alone(orc, index):
+    idx, vals, offs = index
+    lens = np.diff(offs)
+    big = int(np.argmax(lens))           # longest list: its answer bound is huge
+    small = [int(np.argsort(lens)[10]), int(np.argsort(lens)[20])]
+    srv = api.Server(idx, slots=2, max_batch_queries=16, max_terms=8, slot_bytes=1 << 20)
+    try:
+        srv.submit(1, [big])
+        srv.submit(2, small)
+        srv.drain()
+        res = {r[0]: r for r in srv.poll()}
+    finally:
+        srv.close()
+    assert res[1][2] == capi.BP_ERR_SCRATCH
+    assert res[2][2] == capi.BP_OK
+    assert np.array_equal(res[2][5], svs(orc, vals, offs, small))
