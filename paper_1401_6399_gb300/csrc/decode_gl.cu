@@ -8,6 +8,7 @@
 #include "decode.h"
 #include "gl_block.cuh"
 
+
 namespace bp {
 
 namespace {
@@ -15,12 +16,29 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMinBlocks = 5;  // 40 resident warps per SM
 
+
+// Store (or sum) one decoded block: lane l holds positions 16(l%8)+4t+l/8.
 template <bool SUM>
-__device__ __forceinline__ void gl_decode_unit(const GlView &v, uint32_t q, int lane,
-                                               uint32_t *__restrict__ out, uint64_t &acc,
-                                               uint32_t *status) {
-  SuperInfo si;
-  if (!gl_super(v, q, lane, si, status)) return;
+__device__ __forceinline__ void store_block(const uint32_t x[4], uint32_t cnt, int lane,
+                                            uint32_t *__restrict__ o, uint64_t &acc) {
+  if (SUM) {
+#pragma unroll
+    for (int t = 0; t < 4; t++)
+      if ((uint32_t)gl_pos(lane, t) < cnt) acc += x[t];
+  } else if (cnt == 128u) {
+#pragma unroll
+    for (int t = 0; t < 4; t++) o[gl_pos(lane, t)] = x[t];
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; t++)
+      if ((uint32_t)gl_pos(lane, t) < cnt) o[gl_pos(lane, t)] = x[t];
+  }
+}
+
+template <bool SUM>
+__device__ __forceinline__ void gl_decode_unit(const GlView &v, const SuperInfo &si, uint32_t q,
+                                               int lane, uint32_t *__restrict__ out,
+                                               uint64_t &acc) {
   for (uint32_t j = 0; j < si.nblk; j++) {
     const int b = (int)__shfl_sync(kFull, si.b, j);
     const uint32_t F = __shfl_sync(kFull, si.F, j);
@@ -28,22 +46,7 @@ __device__ __forceinline__ void gl_decode_unit(const GlView &v, uint32_t q, int 
     const uint32_t blk = q * 32u + j;
     uint32_t x[4];
     gl_block_values(b, v.payload + woff, F, lane, x);
-    const uint32_t cnt = min(128u, v.n - 128u * blk);
-    if (SUM) {
-#pragma unroll
-      for (int t = 0; t < 4; t++)
-        if ((uint32_t)gl_pos(lane, t) < cnt) acc += x[t];
-    } else {
-      uint32_t *o = out + 128ull * blk;
-      if (cnt == 128u) {
-#pragma unroll
-        for (int t = 0; t < 4; t++) o[gl_pos(lane, t)] = x[t];
-      } else {
-#pragma unroll
-        for (int t = 0; t < 4; t++)
-          if ((uint32_t)gl_pos(lane, t) < cnt) o[gl_pos(lane, t)] = x[t];
-      }
-    }
+    store_block<SUM>(x, min(128u, v.n - 128u * blk), lane, out + 128ull * blk, acc);
   }
 }
 
@@ -88,7 +91,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     if (!ok) continue;
     const uint64_t q = u - base;
     if (q >= v.nsuper) continue;
-    gl_decode_unit<SUM>(v, (uint32_t)q, lane, out + out_off, acc, status);
+    SuperInfo si;
+    if (gl_super(v, (uint32_t)q, lane, si, status))
+      gl_decode_unit<SUM>(v, si, (uint32_t)q, lane, out + out_off, acc);
   }
   if (SUM && cur != 0xFFFFFFFFu) flush_sum(acc, sums + cur, lane);
 }
