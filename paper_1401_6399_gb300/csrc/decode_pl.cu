@@ -1,18 +1,32 @@
 // decode_pl.cu -- decoding of the paper's S4-BP128-D4 layout (PL).
 //
-// Three launches per call (all lists of a batch at once):
-//  1. pl_walk: one warp per list follows the meta-block chain (Section 4.3:
-//     16 width bytes, then 16 blocks of 16b bytes each; then leftover blocks
-//     with one width byte each) and records every block's byte offset and
-//     width.  Work unit u of a list: its block u - unit_base, and one last
-//     unit for the varint tail.
-//  2. pl_decode: tiles of 32 units; each warp unpacks 4 blocks (Algorithm 1,
-//     4-lane interleave), the D4 seed of every block -- the column sums of
-//     all earlier blocks of its list, starting from (0,0,0,0) (Section 5) --
-//     comes from a segmented scan inside the tile and a decoupled look-back
-//     over earlier tiles, then the values are stored (or summed).
-//  3. pl_tail: one warp per list decodes the fewer than 128 final integers
-//     (varint of D1 gaps, Section 4.1) after the last packed value.
+// In this layout only the blocks before a block say where it is: meta-block
+// m+1 starts where meta-block m ends (16 width bytes, then 16 blocks of 16b
+// bytes, Section 4.3), and the D4 seed of a block is the sum of the column
+// deltas of every earlier block of its list (Section 5).  Both sequential
+// dependencies are resolved by parallel passes over all lists of a call:
+//
+//  parse   A stream is read as 16-byte lines, and meta-blocks start on line
+//          boundaries.  Every line is a candidate start: its successor is
+//          line + 1 + (sum of its 16 bytes), or none (a dead line) if a byte
+//          exceeds 32 or the meta-block would run past the stream.  pl_parse
+//          takes segments of kSeg lines; pointer jumping over the live lines
+//          of a segment gives, for each of the kEnt lines where the true
+//          chain can enter it (a meta-block spans at most 513 lines), where
+//          the chain leaves and how many meta-blocks it passed, and a group
+//          of kGrp segments composes these maps.  pl_resolve follows the
+//          group maps of each list from line 1; pl_emit walks every segment
+//          from its entry and records the byte offset and width of each block.
+//  rest    pl_leftover reads the fewer than 16 blocks after the meta-blocks
+//          (one width byte each) and checks the stream's size.
+//  seeds   pl_units<kColsum> sums the deltas of each column over chunks of
+//          kChunk work units; a segmented exclusive scan over the chunks
+//          (every list restarts from zero) gives each chunk its seed.
+//  decode  pl_units<kStore|kSum> unpacks every block (Algorithm 1, 4-lane
+//          interleave) and adds the running column seed; pl_tail decodes the
+//          varint tail (Section 4.1) from the last packed value.
+//
+// Work unit u of a list: its block u - unit_base, then one unit for the tail.
 #include "decode.h"
 #include "pl_block.cuh"
 
@@ -21,327 +35,784 @@ namespace bp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTileUnits = 32;  // 8 warps x 4 units
+constexpr uint32_t kSeg = 4096;     // lines per parse segment
+constexpr uint32_t kEnt = 513;      // lines where a chain can enter a segment
+constexpr uint32_t kGrp = 8;        // segments per group
+constexpr uint32_t kLiveCap = 256;  // live lines kept per segment for pl_emit
+constexpr uint32_t kMapChunk = 16;  // group maps staged at a time by pl_resolve
+constexpr uint32_t kChunk = 32;     // work units per seed chunk
+constexpr uint32_t kScanPer = 16;   // chunks per thread in the chunk scan
+constexpr uint32_t kScanTile = kThreads * kScanPer;
+constexpr int kUnitMinBlocks = 5;  // resident CTAs per SM for pl_units (<= 51 registers)
 constexpr uint64_t kOffMask = (1ull << 56) - 1;
-constexpr uint32_t kBadWidth = 0xFF;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint64_t kBadEntry = ~0ull;  // width byte 0xFF: no block to decode
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kDead = 0xFFFFu;  // chain state: the chain stopped earlier
+
+// A chain state is packed as (entry line offset | meta-blocks passed << 16);
+// a line's jump as (target line - segment start | meta-blocks passed << 16).
+__device__ __forceinline__ uint32_t lo16(uint32_t v) { return v & 0xFFFFu; }
+
+size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Lists with at least one meta-block have at least 17 work units.
+uint64_t max_long_lists(uint64_t units, uint32_t count) {
+  const uint64_t m = units / 17;
+  return m < count ? m : count;
+}
+// A list of nb blocks has at most 32.07 nb + 42 lines, so fewer than
+// nb / 127 + 1.02 segments.
+uint64_t max_segs(uint64_t units, uint32_t count) {
+  return units / 127 + 2 * max_long_lists(units, count) + 1;
+}
+uint64_t max_groups(uint64_t units, uint32_t count) {
+  return max_segs(units, count) / kGrp + max_long_lists(units, count) + 1;
+}
 
 struct PlScratch {
-  uint64_t *boffw;   // [units] byte offset | width << 56 (tail unit: tail offset)
-  uint32_t *ticket;  // tile ticket counter (zeroed per call)
-  uint32_t *flags;   // [ntiles] 0 none, 1|head<<2 aggregate, 2 inclusive (zeroed per call)
-  uint4 *agg;        // [ntiles]
-  uint4 *incl;       // [ntiles]
-  uint32_t *lastval; // [count] last packed value of each list
+  uint64_t *boffw;      // [units] byte offset | width << 56; tail unit: tail offset
+  uint32_t *seg_base;   // [count + 1] first segment of each list; [count]: total
+  uint32_t *grp_base;   // [count + 1] first group of each list; [count]: total
+  uint32_t *ctl;        // [1] nonzero: the lists do not tile the units, do nothing
+  uint32_t *seg_in;     // [segs][kEnt] chain state entering the segment, by group entry
+  uint32_t *live;       // [segs][kLiveCap] live line | successor distance << 16
+  uint32_t *live_cnt;   // [segs]
+  uint32_t *grp_map;    // [groups][kEnt] chain state after the group, by group entry
+  uint32_t *grp_entry;  // [groups] entry line offset of the true chain (kNone: off it)
+  uint32_t *grp_mbase;  // [groups] meta-blocks before the group
+  uint32_t *list_qm;    // [count] line after the last meta-block; 0: the list is bad
+  uint4 *chunk;         // [chunks] column sums, then seeds
+  uint32_t *chunk_head; // [chunks] a list starts inside the chunk
+  uint4 *tile;          // [tiles] segmented tile sums, then tile seeds
+  uint32_t *tile_head;  // [tiles]
+  uint32_t *lastval;    // [count] last packed value of each list
 };
-
-__host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct PlLayout {
-  size_t boffw, ticket, flags, agg, incl, lastval, total;
+  size_t boffw, seg_base, grp_base, ctl, seg_in, live, live_cnt, grp_map, grp_entry, grp_mbase,
+      list_qm, chunk, chunk_head, tile, tile_head, lastval, total;
 };
 
-__host__ __device__ inline PlLayout pl_layout(uint64_t units, uint32_t count) {
-  const uint64_t ntiles = (units + kTileUnits - 1) / kTileUnits;
+PlLayout pl_layout(uint64_t units, uint32_t count) {
+  const uint64_t S = max_segs(units, count), G = max_groups(units, count);
+  const uint64_t nch = (units + kChunk - 1) / kChunk, nt = (nch + kScanTile - 1) / kScanTile;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t r = o;
+    o = a256(o + bytes);
+    return r;
+  };
   PlLayout L;
-  L.boffw = 0;
-  L.ticket = align256(8 * units);
-  L.flags = L.ticket + 16;  // ticket and flags are cleared together
-  L.agg = align256(L.flags + 4 * ntiles);
-  L.incl = L.agg + 16 * ntiles;
-  L.lastval = align256(L.incl + 16 * ntiles);
-  L.total = align256(L.lastval + 4 * (size_t)count);
+  L.boffw = take(8 * units);
+  L.seg_base = take(4 * ((size_t)count + 1));
+  L.grp_base = take(4 * ((size_t)count + 1));
+  L.ctl = take(16);
+  L.seg_in = take(4 * kEnt * S);
+  L.live = take(4 * kLiveCap * S);
+  L.live_cnt = take(4 * S);
+  L.grp_map = take(4 * kEnt * G);
+  L.grp_entry = take(4 * G);
+  L.grp_mbase = take(4 * G);
+  L.list_qm = take(4 * (size_t)count);
+  L.chunk = take(16 * nch);
+  L.chunk_head = take(4 * nch);
+  L.tile = take(16 * nt);
+  L.tile_head = take(4 * nt);
+  L.lastval = take(4 * (size_t)count);
+  L.total = o;
   return L;
+}
+
+PlScratch carve(void *scratch, const PlLayout &L) {
+  uint8_t *b = static_cast<uint8_t *>(scratch);
+  PlScratch sc;
+  sc.boffw = reinterpret_cast<uint64_t *>(b + L.boffw);
+  sc.seg_base = reinterpret_cast<uint32_t *>(b + L.seg_base);
+  sc.grp_base = reinterpret_cast<uint32_t *>(b + L.grp_base);
+  sc.ctl = reinterpret_cast<uint32_t *>(b + L.ctl);
+  sc.seg_in = reinterpret_cast<uint32_t *>(b + L.seg_in);
+  sc.live = reinterpret_cast<uint32_t *>(b + L.live);
+  sc.live_cnt = reinterpret_cast<uint32_t *>(b + L.live_cnt);
+  sc.grp_map = reinterpret_cast<uint32_t *>(b + L.grp_map);
+  sc.grp_entry = reinterpret_cast<uint32_t *>(b + L.grp_entry);
+  sc.grp_mbase = reinterpret_cast<uint32_t *>(b + L.grp_mbase);
+  sc.list_qm = reinterpret_cast<uint32_t *>(b + L.list_qm);
+  sc.chunk = reinterpret_cast<uint4 *>(b + L.chunk);
+  sc.chunk_head = reinterpret_cast<uint32_t *>(b + L.chunk_head);
+  sc.tile = reinterpret_cast<uint4 *>(b + L.tile);
+  sc.tile_head = reinterpret_cast<uint32_t *>(b + L.tile_head);
+  sc.lastval = reinterpret_cast<uint32_t *>(b + L.lastval);
+  return sc;
 }
 
 __device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
 }
 
-// ---- 1. meta-block walk -------------------------------------------------------
+__device__ __forceinline__ uint32_t meta_blocks(const bp_list &L) { return (L.n / 128u) / 16u; }
+
+__device__ __forceinline__ bool header_ok(const uint8_t *enc, const bp_list &L) {
+  return L.enc_bytes >= 16 && (L.enc_offset & 15u) == 0 && rd_u32(enc) == L.n &&
+         rd_u32(enc + 4) == 0u && rd_u32(enc + 12) == 0u;
+}
+
+// Largest i < count with base[i] <= g (the list owning segment or group g).
+__device__ __forceinline__ uint32_t owner(const uint32_t *base, uint32_t count, uint32_t g) {
+  uint32_t lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// ---- plan: segments and groups of every list; the lists must tile the units ---------------
+
+__device__ __forceinline__ uint64_t warp_incl_u64(uint64_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t t = __shfl_up_sync(kFull, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(1024)
+    pl_plan(ListSrc src, uint64_t total_units, uint64_t max_s, uint64_t max_g, PlScratch sc,
+            uint32_t *status) {
+  __shared__ uint64_t s_w[32][3];
+  __shared__ uint64_t s_carry[3];
+  __shared__ uint32_t s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    s_carry[0] = s_carry[1] = s_carry[2] = 0;
+    s_bad = 0;
+  }
+  __syncthreads();
+  for (uint64_t base = 0; base < src.count; base += 1024) {
+    const uint64_t i = base + tid;
+    uint64_t v[3] = {0, 0, 0};  // units, segments, groups
+    bp_list L{};
+    if (i < src.count) {
+      L = src.get((uint32_t)i);
+      v[0] = bp_fmt::units_of(L.n, BP_LAYOUT_PAPER);
+      if (meta_blocks(L) > 0 && L.enc_bytes <= bp_fmt::pl_bound(L.n)) {
+        v[1] = (L.enc_bytes / 16 + kSeg - 1) / kSeg;
+        v[2] = (v[1] + kGrp - 1) / kGrp;
+      }
+    }
+    uint64_t inc[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      inc[k] = warp_incl_u64(v[k], lane);
+      if (lane == 31) s_w[w][k] = inc[k];
+    }
+    __syncthreads();
+    uint64_t ex[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint64_t p = s_carry[k];
+      for (int j = 0; j < w; j++) p += s_w[j][k];
+      ex[k] = p + inc[k] - v[k];
+    }
+    if (i < src.count) {
+      if (L.unit_base != ex[0]) s_bad = 1;
+      sc.seg_base[i] = (uint32_t)ex[1];
+      sc.grp_base[i] = (uint32_t)ex[2];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; k++)
+        for (int j = 0; j < 32; j++) s_carry[k] += s_w[j][k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const bool bad = s_bad || s_carry[0] != total_units || s_carry[1] > max_s ||
+                     s_carry[2] > max_g;
+    sc.seg_base[src.count] = bad ? 0u : (uint32_t)s_carry[1];
+    sc.grp_base[src.count] = bad ? 0u : (uint32_t)s_carry[2];
+    sc.ctl[0] = bad ? 1u : 0u;
+    if (bad) set_status(status, BP_ERR_ARG);
+  }
+}
+
+// ---- parse: segment maps, composed per group -------------------------------------------------
 
 __global__ void __launch_bounds__(kThreads)
-    pl_walk_kernel(const uint8_t *__restrict__ data, ListSrc src, PlScratch sc,
-                   uint64_t out_cap, bool sum, uint32_t *status) {
+    pl_parse(const uint8_t *__restrict__ data, ListSrc src, PlScratch sc) {
+  constexpr int kRounds = kSeg / kThreads;  // lines per thread
+  constexpr int kWarps = kThreads / 32;
+  __shared__ uint32_t s_p[kSeg];
+  __shared__ uint16_t s_live[kSeg];
+  __shared__ uint32_t s_state[kEnt];
+  __shared__ uint32_t s_ball[kRounds * kWarps];
+  __shared__ uint32_t s_pre[kRounds * kWarps];
+  __shared__ uint32_t s_nlive;
+  if (sc.ctl[0]) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  volatile uint32_t *vp = s_p;
+  const uint32_t ngroups = sc.grp_base[src.count];
+  for (uint32_t h = blockIdx.x; h < ngroups; h += gridDim.x) {
+    const uint32_t li = owner(sc.grp_base, src.count, h);
+    const bp_list L = src.get(li);
+    const uint4 *lines = reinterpret_cast<const uint4 *>(data + L.enc_offset);
+    // whole lines of the stream (none if it is misaligned: pl_resolve rejects it)
+    const uint64_t nu = (L.enc_offset & 15u) ? 0 : L.enc_bytes / 16;
+    const uint32_t sb = sc.seg_base[li];
+    const uint32_t nseg = sc.seg_base[li + 1] - sb;
+    const uint32_t ls0 = (h - sc.grp_base[li]) * kGrp;
+    const uint32_t ls1 = min(ls0 + kGrp, nseg);
+    for (uint32_t x = tid; x < kEnt; x += kThreads) s_state[x] = x;
+    __syncthreads();
+    for (uint32_t ls = ls0; ls < ls1; ls++) {
+      const uint32_t g = sb + ls;
+      const uint64_t u0 = (uint64_t)ls * kSeg;
+      for (uint32_t x = tid; x < kEnt; x += kThreads) sc.seg_in[(size_t)g * kEnt + x] = s_state[x];
+      // one step from every line
+      uint32_t livemask = 0;
+#pragma unroll 4
+      for (int r = 0; r < kRounds; r++) {
+        const uint32_t i = r * kThreads + tid;
+        const uint64_t u = u0 + i;
+        uint32_t p = i;  // dead: stays put, no meta-block
+        if (u >= 1 && u < nu) {
+          const uint4 v = __ldg(lines + u);
+          const uint32_t big = __vcmpgtu4(v.x, 0x20202020u) | __vcmpgtu4(v.y, 0x20202020u) |
+                               __vcmpgtu4(v.z, 0x20202020u) | __vcmpgtu4(v.w, 0x20202020u);
+          const uint32_t sum =
+              __dp4a(v.x, 0x01010101u,
+                     __dp4a(v.y, 0x01010101u, __dp4a(v.z, 0x01010101u, __dp4a(v.w, 0x01010101u, 0u))));
+          if (big == 0u && u + 1 + sum <= nu) {
+            p = (i + 1 + sum) | (1u << 16);
+            livemask |= 1u << r;
+          }
+        }
+        s_p[i] = p;
+        const uint32_t bal = __ballot_sync(kFull, (livemask >> r) & 1u);
+        if (lane == 0) s_ball[r * kWarps + w] = bal;
+      }
+      __syncthreads();
+      if (w == 0) {  // exclusive prefix of the live counts in (round, warp) order
+        uint32_t c[4], t = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          c[k] = __popc(s_ball[4 * lane + k]);
+          t += c[k];
+        }
+        uint32_t inc = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, inc, d);
+          if (lane >= d) inc += y;
+        }
+        uint32_t ex = inc - t;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          s_pre[4 * lane + k] = ex;
+          ex += c[k];
+        }
+        if (lane == 31) s_nlive = inc;
+      }
+      __syncthreads();
+      const uint32_t nlive = s_nlive;
+      uint32_t *gl_live = sc.live + (size_t)g * kLiveCap;
+#pragma unroll 4
+      for (int r = 0; r < kRounds; r++) {
+        if ((livemask >> r) & 1u) {
+          const uint32_t i = r * kThreads + tid;
+          const uint32_t rank =
+              s_pre[r * kWarps + w] + __popc(s_ball[r * kWarps + w] & lanemask_lt(lane));
+          s_live[rank] = (uint16_t)i;
+          if (nlive <= kLiveCap) gl_live[rank] = i | ((lo16(s_p[i]) - i) << 16);
+        }
+      }
+      if (tid == 0) sc.live_cnt[g] = nlive;
+      __syncthreads();
+      // pointer jumping over the live lines (in place: every value read is a
+      // consistent (target, count) pair, so rounds only converge faster)
+      for (int round = 0; round < 16; round++) {
+        int changed = 0;
+        for (uint32_t k = tid; k < nlive; k += kThreads) {
+          const uint32_t i = s_live[k];
+          const uint32_t p = vp[i];
+          const uint32_t a = lo16(p);
+          if (a < kSeg) {
+            const uint32_t q = vp[a];
+            const uint32_t np = lo16(q) | ((p & 0xFFFF0000u) + (q & 0xFFFF0000u));
+            if (np != p) {
+              vp[i] = np;
+              changed = 1;
+            }
+          }
+        }
+        if (!__syncthreads_or(changed)) break;
+      }
+      // compose the group's map with this segment's
+      for (uint32_t x = tid; x < kEnt; x += kThreads) {
+        const uint32_t st = s_state[x];
+        const uint32_t off = lo16(st);
+        if (off != kDead) {
+          const uint32_t p = s_p[off];
+          const uint32_t nr = lo16(p);
+          const uint32_t cnt = (st >> 16) + (p >> 16);
+          s_state[x] = (nr >= kSeg ? nr - kSeg : kDead) | (cnt << 16);
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t x = tid; x < kEnt; x += kThreads) sc.grp_map[(size_t)h * kEnt + x] = s_state[x];
+    __syncthreads();
+  }
+}
+
+// ---- resolve: the true chain through the groups of each list ----------------------------------
+
+__global__ void __launch_bounds__(kThreads)
+    pl_resolve(const uint8_t *__restrict__ data, ListSrc src, PlScratch sc, uint32_t *status) {
+  __shared__ uint32_t s_map[kMapChunk * kEnt];
+  __shared__ uint32_t s_e, s_m, s_st;  // s_st: 0 walking, 1 done, 2 bad
+  if (sc.ctl[0]) return;
+  const int tid = threadIdx.x;
+  for (uint32_t li = blockIdx.x; li < src.count; li += gridDim.x) {
+    const bp_list L = src.get(li);
+    const uint32_t M = meta_blocks(L);
+    const uint32_t h0 = sc.grp_base[li], h1 = sc.grp_base[li + 1];
+    if (tid == 0) {
+      s_e = 1;  // the first meta-block follows the 16-byte header
+      s_m = 0;
+      s_st = !header_ok(data + L.enc_offset, L) ? 2u : (M == 0 ? 1u : 0u);
+    }
+    __syncthreads();
+    for (uint32_t hc = h0; hc < h1; hc += kMapChunk) {
+      const uint32_t nh = min(kMapChunk, h1 - hc);
+      if (s_st == 0)
+        for (uint32_t k = tid; k < nh * kEnt; k += kThreads)
+          s_map[k] = sc.grp_map[(size_t)hc * kEnt + k];
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t e = s_e, m = s_m, st = s_st;
+        for (uint32_t j = 0; j < nh; j++) {
+          const uint32_t h = hc + j;
+          if (st != 0) {
+            sc.grp_entry[h] = kNone;
+            continue;
+          }
+          const uint32_t p = s_map[j * kEnt + e];
+          sc.grp_entry[h] = e;
+          sc.grp_mbase[h] = m;
+          m += p >> 16;
+          if (m >= M) st = 1;
+          else if (lo16(p) == kDead) st = 2;
+          else e = lo16(p);
+        }
+        s_e = e;
+        s_m = m;
+        s_st = st;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const bool ok = s_st == 1;
+      if (!ok) set_status(status, BP_ERR_CORRUPT);
+      sc.list_qm[li] = ok ? (M == 0 ? 1u : kNone) : 0u;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- emit: block offsets and widths of every meta-block -----------------------------------
+
+// One lane: the 16 blocks of the meta-block at `line`.
+__device__ __forceinline__ void emit_meta(const uint4 *lines, uint64_t line, uint64_t *dst) {
+  const uint4 v = __ldg(lines + line);
+  const uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+  uint64_t off = 16ull * (line + 1);
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    const uint32_t b = (wds[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+    dst[j] = off | ((uint64_t)b << 56);
+    off += 16ull * b;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    pl_emit(const uint8_t *__restrict__ data, ListSrc src, PlScratch sc, uint32_t *status) {
+  if (sc.ctl[0]) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
+  const uint32_t nsegs = sc.seg_base[src.count];
+  for (uint32_t g = warp; g < nsegs; g += nwarps) {
+    const uint32_t li = owner(sc.seg_base, src.count, g);
+    if (sc.list_qm[li] == 0u) continue;
+    const uint32_t ls = g - sc.seg_base[li];
+    const uint32_t h = sc.grp_base[li] + ls / kGrp;
+    const uint32_t x = sc.grp_entry[h];
+    if (x == kNone) continue;
+    const uint32_t st = sc.seg_in[(size_t)g * kEnt + x];
+    if (lo16(st) == kDead) continue;
+    const bp_list L = src.get(li);
+    const uint32_t M = meta_blocks(L);
+    const uint32_t mb = sc.grp_mbase[h] + (st >> 16);
+    if (mb >= M) continue;
+    const uint32_t need = M - mb;
+    const uint4 *lines = reinterpret_cast<const uint4 *>(data + L.enc_offset);
+    const uint64_t nu = L.enc_bytes / 16;
+    const uint64_t u0 = (uint64_t)ls * kSeg;
+    uint64_t *dst = sc.boffw + L.unit_base + 16ull * mb;
+    uint32_t t = lo16(st), done = 0;
+    bool fail = false;
+    const uint32_t nlive = sc.live_cnt[g];
+    if (nlive <= kLiveCap) {
+      // the live lines, in order, 32 at a time: find the chain's nodes among them
+      const uint32_t *lv = sc.live + (size_t)g * kLiveCap;
+      for (uint32_t p0 = 0; p0 < nlive && t < kSeg && done < need; p0 += 32) {
+        const uint32_t e = p0 + lane < nlive ? lv[p0 + lane] : kNone;
+        const uint32_t line = lo16(e);  // padding 0xFFFF never equals t < kSeg
+        bool node = false;
+        const uint32_t before = done;
+        for (int it = 0; it < 32 && done < need; it++) {
+          const uint32_t m = __ballot_sync(kFull, line == t);
+          if (!m) break;
+          const int sl = __ffs(m) - 1;
+          node |= lane == sl;
+          t += __shfl_sync(kFull, e >> 16, sl);
+          done++;
+        }
+        const uint32_t nm = __ballot_sync(kFull, node);
+        if (node) emit_meta(lines, u0 + line, dst + 16ull * (before + __popc(nm & lanemask_lt(lane))));
+      }
+    } else {
+      // more live lines than kept: read each node's width line from the stream
+      for (uint32_t it = 0; t < kSeg && done < need && it < kSeg; it++) {
+        const uint64_t line = u0 + t;
+        if (line >= nu) {
+          fail = true;
+          break;
+        }
+        const uint32_t wb = lane < 16 ? reinterpret_cast<const uint8_t *>(lines)[16 * line + lane] : 0u;
+        if (__any_sync(kFull, wb > 32u)) {
+          fail = true;
+          break;
+        }
+        uint32_t inc = wb;
+#pragma unroll
+        for (int d = 1; d < 16; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, inc, d);
+          if (lane >= d) inc += y;
+        }
+        const uint32_t tot = __shfl_sync(kFull, inc, 15);
+        if (line + 1 + tot > nu) {
+          fail = true;
+          break;
+        }
+        if (lane < 16)
+          dst[16ull * done + lane] = (16ull * (line + 1) + 16ull * (inc - wb)) | ((uint64_t)wb << 56);
+        t += 1 + tot;
+        done++;
+      }
+    }
+    if (done == need) {
+      if (lane == 0) sc.list_qm[li] = (uint32_t)(u0 + t);
+    } else if (t < kSeg || fail) {
+      // the segment maps promised a longer chain: the stream changed under us
+      if (lane == 0) {
+        set_status(status, BP_ERR_CORRUPT);
+        sc.list_qm[li] = 0u;
+      }
+    }
+  }
+}
+
+// ---- leftover blocks and the tail position ---------------------------------------------
+
+__global__ void __launch_bounds__(kThreads)
+    pl_leftover(const uint8_t *__restrict__ data, ListSrc src, PlScratch sc, uint64_t out_cap,
+                bool sum, uint32_t *status) {
+  if (sc.ctl[0]) return;
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
   for (uint32_t li = warp; li < src.count; li += nwarps) {
     const bp_list L = src.get(li);
     const uint8_t *enc = data + L.enc_offset;
-    const uint64_t bytes = L.enc_bytes;
-    const uint64_t U0 = L.unit_base;
-    const uint32_t nb = L.n / 128u, meta = nb / 16u;
-    if (!sum && L.out_offset + L.n > out_cap) {
-      if (lane == 0) set_status(status, BP_ERR_CAPACITY);
-      for (uint32_t j = lane; j <= nb; j += 32) sc.boffw[U0 + j] = (uint64_t)kBadWidth << 56;
-      continue;
+    const uint64_t bytes = L.enc_bytes, U0 = L.unit_base;
+    const uint32_t nb = L.n / 128u;
+    const uint32_t qm = sc.list_qm[li];
+    bool ok = qm != 0u && qm != kNone;
+    uint32_t why = BP_ERR_CORRUPT;
+    if (ok && !sum && L.out_offset + L.n > out_cap) {
+      ok = false;
+      why = BP_ERR_CAPACITY;
     }
-    bool ok = bytes >= 16 && (L.enc_offset & 15u) == 0;
-    uint32_t tail_bytes = 0;
-    if (ok) {
-      ok = rd_u32(enc) == L.n && rd_u32(enc + 4) == 0u && rd_u32(enc + 12) == 0u;
-      tail_bytes = rd_u32(enc + 8);
-    }
-    uint64_t pos = 16;
-    uint32_t k = 0;  // blocks recorded so far
-    for (uint32_t m = 0; ok && m < meta; m++) {
-      if (pos + 16 > bytes) {
-        ok = false;
-        break;
-      }
-      const uint32_t w = lane < 16 ? enc[pos + lane] : 0u;
-      if (__any_sync(kFull, w > 32u)) {
-        ok = false;
-        break;
-      }
-      uint32_t incl = 16u * w;
-#pragma unroll
-      for (int dd = 1; dd < 16; dd <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, dd);
-        if (lane >= dd) incl += t;
-      }
-      const uint64_t next = pos + 16 + __shfl_sync(kFull, incl, 15);
-      if (next > bytes) {  // the meta-block runs past the stream
-        ok = false;
-        break;
-      }
-      const uint64_t blk_off = pos + 16 + (incl - 16u * w);
-      if (lane < 16) sc.boffw[U0 + k + lane] = blk_off | ((uint64_t)w << 56);
-      pos = next;
-      k += 16;
-    }
-    for (; ok && k < nb; k++) {
+    uint64_t pos = 16ull * qm;
+    for (uint32_t k = 16u * meta_blocks(L); ok && k < nb; k++) {
       if (pos + 1 > bytes) {
         ok = false;
         break;
       }
-      const uint32_t w = enc[pos];
-      if (w > 32u || pos + 1 + 16ull * w > bytes) {
+      const uint32_t wd = enc[pos];
+      if (wd > 32u || pos + 1 + 16ull * wd > bytes) {
         ok = false;
         break;
       }
-      if (lane == 0) sc.boffw[U0 + k] = (pos + 1) | ((uint64_t)w << 56);
-      pos += 1 + 16ull * w;
+      if (lane == 0) sc.boffw[U0 + k] = (pos + 1) | ((uint64_t)wd << 56);
+      pos += 1 + 16ull * wd;
     }
-    if (ok && pos + tail_bytes != bytes) ok = false;
+    if (ok && pos + rd_u32(enc + 8) != bytes) ok = false;
     if (ok) {
       if (lane == 0) sc.boffw[U0 + nb] = pos;
     } else {
-      if (lane == 0) set_status(status, BP_ERR_CORRUPT);
-      for (uint32_t j = k + lane; j <= nb; j += 32) sc.boffw[U0 + j] = (uint64_t)kBadWidth << 56;
+      if (lane == 0) {
+        set_status(status, why);
+        sc.list_qm[li] = 0u;
+      }
+      for (uint32_t j = lane; j <= nb; j += 32) sc.boffw[U0 + j] = kBadEntry;
     }
   }
 }
 
-// ---- 2. decode with decoupled look-back ------------------------------------------
+// ---- column sums and decode over chunks of work units -----------------------------------
 
-__device__ __forceinline__ uint32_t ld_flag(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_flag(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
+enum { kColsum = 0, kStore = 1, kSum = 2 };
 
 __device__ __forceinline__ uint32_t comp(const uint4 &v, int s) {
   return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
 }
 
-template <bool SUM>
-__global__ void __launch_bounds__(kThreads, 4)
-    pl_decode_kernel(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
-                     uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t *status) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_wsum[8][4];  // warp aggregate per column
-  __shared__ uint32_t s_whead[8];
-  __shared__ uint4 s_E;
-
-  if (threadIdx.x == 0) s_tile = atomicAdd(sc.ticket, 1u);
-  __syncthreads();
-  const uint64_t t = s_tile;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s = lane >> 3, c = lane & 7;
-
-  uint32_t xv[4][4];   // local running sums down the lane's 4 rows, per unit
-  uint32_t cex[4];     // exclusive sum over lanes c' < c of the column, per unit
-  uint32_t cs[4];      // column total of the block (own column), per unit
-  bool head[4], isblk[4];
-  uint32_t lst[4], kb[4];
-
+__device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane) {
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const uint64_t u = t * kTileUnits + 4u * w + i;
-    head[i] = false;
-    isblk[i] = false;
-    cs[i] = 0;
-    cex[i] = 0;
-    lst[i] = 0xFFFFFFFFu;
-    kb[i] = 0;
-#pragma unroll
-    for (int j = 0; j < 4; j++) xv[i][j] = 0;
-    if (u >= total_units) continue;
-    const uint32_t li = src.find(u);
-    const bp_list L = src.get(li);
-    const uint64_t k = u - L.unit_base;
-    const uint32_t nb = L.n / 128u;
-    lst[i] = li;
-    kb[i] = (uint32_t)k;
-    head[i] = (k == 0);
-    if (k >= nb) continue;
-    const uint64_t e = sc.boffw[u];
-    const uint32_t b = (uint32_t)(e >> 56);
-    if (b > 32u) continue;  // list marked bad by the walk: nothing is stored
-    isblk[i] = true;
-    uint32_t d[4];
-    pl_block_deltas((int)b, data + L.enc_offset + (e & kOffMask), lane, d);
-    xv[i][0] = d[0];
-    xv[i][1] = d[0] + d[1];
-    xv[i][2] = xv[i][1] + d[2];
-    xv[i][3] = xv[i][2] + d[3];
-    uint32_t incl = xv[i][3];
-#pragma unroll
-    for (int dd = 1; dd < 8; dd <<= 1) {
-      const uint32_t v = __shfl_up_sync(kFull, incl, dd, 8);
-      if (c >= dd) incl += v;
-    }
-    cex[i] = incl - xv[i][3];
-    cs[i] = __shfl_sync(kFull, incl, (lane & ~7) | 7);
-  }
-
-  // segmented scan of the 4 units inside the warp (heads restart at zero)
-  uint32_t pw[4];  // exclusive within warp
-  uint32_t r = 0;
-  bool whead = false;
-#pragma unroll
-  for (int i = 0; i < 4; i++) {
-    if (head[i]) {
-      r = 0;
-      whead = true;
-    }
-    pw[i] = r;
-    r += cs[i];
-  }
-  if (c == 0) s_wsum[w][s] = r;
-  if (lane == 0) s_whead[w] = whead ? 1u : 0u;
-  __syncthreads();
-
-  // exclusive within tile for this warp, and whether a head came before it
-  uint32_t W = 0;
-  bool head_before = false;
-  for (int v = 0; v < w; v++) {
-    if (s_whead[v]) {
-      W = s_wsum[v][s];
-      head_before = true;
-    } else {
-      W += s_wsum[v][s];
-    }
-  }
-
-  if (threadIdx.x == 0) {
-    uint4 tail = make_uint4(0, 0, 0, 0);
-    bool th = false;
-    for (int v = 0; v < 8; v++) {
-      if (s_whead[v]) {
-        tail = make_uint4(s_wsum[v][0], s_wsum[v][1], s_wsum[v][2], s_wsum[v][3]);
-        th = true;
-      } else {
-        tail.x += s_wsum[v][0];
-        tail.y += s_wsum[v][1];
-        tail.z += s_wsum[v][2];
-        tail.w += s_wsum[v][3];
-      }
-    }
-    uint4 E = make_uint4(0, 0, 0, 0);
-    if (t > 0) {
-      // publish the aggregate, then look back
-      sc.agg[t] = tail;
-      __threadfence();
-      st_flag(sc.flags + t, 1u | (th ? 4u : 0u));
-      for (int64_t j = (int64_t)t - 1; j >= 0; j--) {
-        uint32_t f = 0, spins = 0;
-        while ((f = ld_flag(sc.flags + j)) == 0u) {
-          if (++spins > kSpinLimit) break;
-          __nanosleep(64);
-        }
-        if (f == 0u) {
-          set_status(status, BP_ERR_TIMEOUT);
-          break;
-        }
-        if (f == 2u) {
-          const uint4 v = __ldcg(sc.incl + j);
-          E.x += v.x; E.y += v.y; E.z += v.z; E.w += v.w;
-          break;
-        }
-        const uint4 v = __ldcg(sc.agg + j);
-        E.x += v.x; E.y += v.y; E.z += v.z; E.w += v.w;
-        if (f & 4u) break;
-      }
-    }
-    uint4 inc = tail;
-    if (!th) {
-      inc.x += E.x; inc.y += E.y; inc.z += E.z; inc.w += E.w;
-    }
-    sc.incl[t] = inc;
-    __threadfence();
-    st_flag(sc.flags + t, 2u);
-    s_E = E;
-  }
-  __syncthreads();
-  const uint32_t Es = comp(s_E, s);
-
-  // seeds and output (list changes are warp-uniform, so sums reduce per warp)
-  auto flush = [&](uint64_t &a, uint32_t li) {
-#pragma unroll
-    for (int dd = 16; dd > 0; dd >>= 1) a += __shfl_down_sync(kFull, a, dd);
-    if (lane == 0 && a) atomicAdd(reinterpret_cast<unsigned long long *>(sums + li), a);
-    a = 0;
-  };
-  uint64_t acc = 0;
-  uint32_t acc_list = 0xFFFFFFFFu;
-  bool head_in_warp = false;
-#pragma unroll
-  for (int i = 0; i < 4; i++) {
-    if (lst[i] == 0xFFFFFFFFu) continue;
-    if (head[i]) head_in_warp = true;
-    uint32_t seed = pw[i];
-    if (!head_in_warp) {
-      seed += W;
-      if (!head_before) seed += Es;
-    }
-    if (head[i]) seed = 0;
-    const bp_list L = src.get(lst[i]);
-    if (!isblk[i]) {
-      // tail unit: its seed's column 3 is the last packed value of the list
-      if (kb[i] == L.n / 128u && s == 3 && c == 0) sc.lastval[lst[i]] = seed;
-      continue;
-    }
-    const uint32_t base = seed + cex[i];
-    if (SUM) {
-      if (acc_list != lst[i]) {
-        if (acc_list != 0xFFFFFFFFu) flush(acc, acc_list);
-        acc_list = lst[i];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++) acc += base + xv[i][j];
-    } else {
-      uint32_t *o = out + L.out_offset + 128ull * kb[i] + 16 * c + s;
-#pragma unroll
-      for (int j = 0; j < 4; j++) o[4 * j] = base + xv[i][j];
-    }
-  }
-  if (SUM && acc_list != 0xFFFFFFFFu) flush(acc, acc_list);
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(kFull, acc, d);
+  if (lane == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long *>(dst), acc);
+  acc = 0;
 }
 
-// ---- 3. varint tail ----------------------------------------------------------------
+// Lane l = 8s + c owns column s, rows 4c..4c+3 of each block (positions
+// 16c + 4j + s); `carry` is the running D4 seed of its column.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
+    pl_units(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
+             uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t *status) {
+  if (sc.ctl[0]) return;
+  const int lane = threadIdx.x & 31, s = lane >> 3, c = lane & 7;
+  const uint64_t warp = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kThreads) >> 5;
+  const uint64_t nch = (total_units + kChunk - 1) / kChunk;
+  uint64_t acc = 0;
+  uint32_t acc_list = kNone;
+  for (uint64_t ch = warp; ch < nch; ch += nwarps) {
+    const uint64_t u0 = ch * kChunk;
+    const uint32_t cnt = total_units - u0 < kChunk ? (uint32_t)(total_units - u0) : kChunk;
+    const uint64_t eL = (uint32_t)lane < cnt ? sc.boffw[u0 + lane] : kBadEntry;
+    uint32_t li = src.find(u0);
+    bp_list L = src.get(li);
+    uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+    uint32_t carry = 0;
+    if (MODE != kColsum) carry = comp(sc.chunk[ch], s);
+    bool head = false;
+    for (uint32_t j = 0; j < cnt; j++) {
+      const uint64_t u = u0 + j;
+      if (u == nxt) {
+        li++;
+        L = src.get(li);
+        nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+      }
+      const uint64_t k = u - L.unit_base;
+      if (k == 0) {
+        carry = 0;
+        head = true;
+      }
+      const uint64_t e = __shfl_sync(kFull, eL, j);
+      if (k >= L.n / 128u) {  // the tail unit: column 3 holds the last packed value
+        if (MODE != kColsum && lane == 24) sc.lastval[li] = carry;
+        continue;
+      }
+      const uint32_t b = (uint32_t)(e >> 56);
+      if (b > 32u) {
+        if (MODE == kColsum && lane == 0 && sc.list_qm[li] != 0u) set_status(status, BP_ERR_CORRUPT);
+        continue;
+      }
+      uint32_t d[4];
+      pl_block_deltas((int)b, data + L.enc_offset + (e & kOffMask), lane, d);
+      if (MODE == kColsum) {
+        carry += d[0] + d[1] + d[2] + d[3];
+        continue;
+      }
+      uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
+      uint32_t inc = x3;
+#pragma unroll
+      for (int dd = 1; dd < 8; dd <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+        if (c >= dd) inc += t;
+      }
+      const uint32_t base = carry + inc - x3;
+      x0 += base;
+      x1 += base;
+      x2 += base;
+      x3 += base;
+      carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
+      if (MODE == kSum) {
+        if (acc_list != li) {
+          if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
+          acc_list = li;
+        }
+        acc += (uint64_t)x0 + x1 + x2 + x3;
+      } else {
+        uint32_t *o = out + L.out_offset + 128ull * k + 16 * c + s;
+        o[0] = x0;
+        o[4] = x1;
+        o[8] = x2;
+        o[12] = x3;
+      }
+    }
+    if (MODE == kColsum) {
+      carry += __shfl_xor_sync(kFull, carry, 1);
+      carry += __shfl_xor_sync(kFull, carry, 2);
+      carry += __shfl_xor_sync(kFull, carry, 4);
+      const uint32_t c1 = __shfl_sync(kFull, carry, 8), c2 = __shfl_sync(kFull, carry, 16),
+                     c3 = __shfl_sync(kFull, carry, 24);
+      if (lane == 0) {
+        sc.chunk[ch] = make_uint4(carry, c1, c2, c3);
+        sc.chunk_head[ch] = head ? 1u : 0u;
+      }
+    }
+  }
+  if (MODE == kSum && acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
+}
+
+// ---- segmented exclusive scan of the chunk sums ---------------------------------------------
+
+struct SegV {
+  uint4 v;
+  uint32_t h;  // a list starts inside: the sum restarts there
+};
+
+__device__ __forceinline__ uint4 add4(const uint4 &a, const uint4 &b) {
+  return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ SegV seg_op(const SegV &a, const SegV &b) {
+  SegV r;
+  r.v = b.h ? b.v : add4(a.v, b.v);
+  r.h = a.h | b.h;
+  return r;
+}
+
+__device__ __forceinline__ SegV seg_zero() {
+  SegV r;
+  r.v = make_uint4(0, 0, 0, 0);
+  r.h = 0;
+  return r;
+}
+
+__device__ __forceinline__ SegV seg_shfl_up(const SegV &a, int d) {
+  SegV r;
+  r.v.x = __shfl_up_sync(kFull, a.v.x, d);
+  r.v.y = __shfl_up_sync(kFull, a.v.y, d);
+  r.v.z = __shfl_up_sync(kFull, a.v.z, d);
+  r.v.w = __shfl_up_sync(kFull, a.v.w, d);
+  r.h = __shfl_up_sync(kFull, a.h, d);
+  return r;
+}
+
+// CTA-wide exclusive segmented scan; `total` receives the CTA's aggregate.
+template <int NT>
+__device__ __forceinline__ SegV cta_excl_scan(const SegV &x, SegV &total) {
+  __shared__ SegV s_w[NT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  SegV inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const SegV y = seg_shfl_up(inc, d);
+    if (lane >= d) inc = seg_op(y, inc);
+  }
+  SegV ex = seg_shfl_up(inc, 1);
+  if (lane == 0) ex = seg_zero();
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  SegV pre = seg_zero(), tot = seg_zero();
+  for (int i = 0; i < NT / 32; i++) {
+    if (i == w) pre = tot;
+    tot = seg_op(tot, s_w[i]);
+  }
+  total = tot;
+  __syncthreads();
+  return seg_op(pre, ex);
+}
+
+__device__ __forceinline__ SegV chunk_val(const PlScratch &sc, uint64_t i) {
+  SegV r;
+  r.v = sc.chunk[i];
+  r.h = sc.chunk_head[i];
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads) pl_scan_reduce(uint64_t nch, PlScratch sc) {
+  if (sc.ctl[0]) return;
+  const uint64_t t = blockIdx.x, base = t * kScanTile + (uint64_t)threadIdx.x * kScanPer;
+  SegV a = seg_zero();
+  for (uint32_t i = 0; i < kScanPer; i++)
+    if (base + i < nch) a = seg_op(a, chunk_val(sc, base + i));
+  SegV tot;
+  cta_excl_scan<kThreads>(a, tot);
+  if (threadIdx.x == 0) {
+    sc.tile[t] = tot.v;
+    sc.tile_head[t] = tot.h;
+  }
+}
+
+__global__ void __launch_bounds__(1024) pl_scan_top(uint64_t ntiles, PlScratch sc) {
+  if (sc.ctl[0]) return;
+  SegV carry = seg_zero();
+  for (uint64_t base = 0; base < ntiles; base += 1024) {
+    const uint64_t i = base + threadIdx.x;
+    SegV x = seg_zero();
+    if (i < ntiles) {
+      x.v = sc.tile[i];
+      x.h = sc.tile_head[i];
+    }
+    SegV tot;
+    const SegV ex = cta_excl_scan<1024>(x, tot);
+    if (i < ntiles) sc.tile[i] = seg_op(carry, ex).v;
+    carry = seg_op(carry, tot);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) pl_scan_down(uint64_t nch, PlScratch sc) {
+  if (sc.ctl[0]) return;
+  const uint64_t t = blockIdx.x, base = t * kScanTile + (uint64_t)threadIdx.x * kScanPer;
+  SegV a[kScanPer];
+  SegV agg = seg_zero();
+#pragma unroll
+  for (uint32_t i = 0; i < kScanPer; i++) {
+    a[i] = base + i < nch ? chunk_val(sc, base + i) : seg_zero();
+    agg = seg_op(agg, a[i]);
+  }
+  SegV tot, r;
+  const SegV ex = cta_excl_scan<kThreads>(agg, tot);
+  r.v = sc.tile[t];
+  r.h = 0;
+  r = seg_op(r, ex);
+#pragma unroll
+  for (uint32_t i = 0; i < kScanPer; i++) {
+    if (base + i < nch) sc.chunk[base + i] = r.v;
+    r = seg_op(r, a[i]);
+  }
+}
+
+// ---- varint tail -----------------------------------------------------------------------------
 
 template <bool SUM>
 __global__ void __launch_bounds__(kThreads)
-    pl_tail_kernel(const uint8_t *__restrict__ data, ListSrc src, uint32_t *__restrict__ out,
-                   uint64_t *sums, PlScratch sc, uint32_t *status) {
-  __shared__ uint8_t s_bytes[8][640];
+    pl_tail(const uint8_t *__restrict__ data, ListSrc src, uint32_t *__restrict__ out,
+            uint64_t *sums, PlScratch sc, uint32_t *status) {
+  __shared__ uint8_t s_bytes[kThreads / 32][640];
+  if (sc.ctl[0]) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t warp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
@@ -349,7 +820,7 @@ __global__ void __launch_bounds__(kThreads)
     const bp_list L = src.get(li);
     const uint32_t nb = L.n / 128u, np = 128u * nb, nt = L.n - np;
     const uint64_t e = sc.boffw[L.unit_base + nb];
-    if (nt == 0 || (e >> 56) == kBadWidth) continue;
+    if (nt == 0 || e == kBadEntry) continue;
     const uint8_t *enc = data + L.enc_offset;
     const uint32_t tail_bytes = rd_u32(enc + 8);
     if (tail_bytes > 5u * nt) {
@@ -385,17 +856,16 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-PlScratch carve(void *scratch, uint64_t units, uint32_t count) {
-  const PlLayout L = pl_layout(units, count);
-  uint8_t *b = static_cast<uint8_t *>(scratch);
-  PlScratch sc;
-  sc.boffw = reinterpret_cast<uint64_t *>(b + L.boffw);
-  sc.ticket = reinterpret_cast<uint32_t *>(b + L.ticket);
-  sc.flags = reinterpret_cast<uint32_t *>(b + L.flags);
-  sc.agg = reinterpret_cast<uint4 *>(b + L.agg);
-  sc.incl = reinterpret_cast<uint4 *>(b + L.incl);
-  sc.lastval = reinterpret_cast<uint32_t *>(b + L.lastval);
-  return sc;
+template <class K>
+int resident_grid(K kernel, int &per_sm_cache) {
+  if (per_sm_cache < 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    per_sm_cache = nb;
+  }
+  return per_sm_cache * device_sm_count();
 }
 
 }  // namespace
@@ -408,23 +878,41 @@ int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
                      uint32_t *out, uint64_t out_cap, uint64_t *sums, void *scratch,
                      size_t scratch_bytes, uint32_t *status, cudaStream_t s) {
   if (total_units == 0 || src.count == 0) return BP_OK;
+  const uint64_t S = max_segs(total_units, src.count), G = max_groups(total_units, src.count);
+  if (S >= 0xFFFFFFFFull || G >= 0xFFFFFFFFull) return BP_ERR_ARG;
   if (!scratch || scratch_bytes < pl_scratch_bytes(total_units, src.count)) return BP_ERR_SCRATCH;
   const PlLayout L = pl_layout(total_units, src.count);
-  const PlScratch sc = carve(scratch, total_units, src.count);
-  const uint64_t ntiles = (total_units + kTileUnits - 1) / kTileUnits;
-  if (cudaMemsetAsync(static_cast<uint8_t *>(scratch) + L.ticket, 0, L.agg - L.ticket, s) !=
-      cudaSuccess)
-    return BP_ERR_CUDA;
-  const int wgrid = (int)std::min<uint64_t>((src.count + 7) / 8, 4096);
-  pl_walk_kernel<<<wgrid, kThreads, 0, s>>>(data, src, sc, out_cap, sums != nullptr, status);
+  const PlScratch sc = carve(scratch, L);
+  const uint64_t nch = (total_units + kChunk - 1) / kChunk;
+  const uint64_t ntiles = (nch + kScanTile - 1) / kScanTile;
+  const int sms = device_sm_count();
+  static int occ_col = -1, occ_store = -1, occ_sum = -1;
+  const uint64_t want_warps = nch;
+  auto unit_grid = [&](int resident) {
+    return (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((want_warps + kThreads / 32 - 1) / (kThreads / 32), resident));
+  };
+  const int lgrid = (int)std::min<uint64_t>((src.count + 7) / 8, 4096);
+  if (cudaMemsetAsync(sc.boffw, 0xFF, 8 * total_units, s) != cudaSuccess) return BP_ERR_CUDA;
+  pl_plan<<<1, 1024, 0, s>>>(src, total_units, S, G, sc, status);
+  pl_parse<<<8 * sms, kThreads, 0, s>>>(data, src, sc);
+  pl_resolve<<<(int)std::min<uint64_t>(src.count, 4ull * sms), kThreads, 0, s>>>(data, src, sc,
+                                                                                   status);
+  pl_emit<<<8 * sms, kThreads, 0, s>>>(data, src, sc, status);
+  pl_leftover<<<lgrid, kThreads, 0, s>>>(data, src, sc, out_cap, sums != nullptr, status);
+  pl_units<kColsum><<<unit_grid(resident_grid(pl_units<kColsum>, occ_col)), kThreads, 0, s>>>(
+      data, src, total_units, out, sums, sc, status);
+  pl_scan_reduce<<<(unsigned)ntiles, kThreads, 0, s>>>(nch, sc);
+  pl_scan_top<<<1, 1024, 0, s>>>(ntiles, sc);
+  pl_scan_down<<<(unsigned)ntiles, kThreads, 0, s>>>(nch, sc);
   if (sums) {
-    pl_decode_kernel<true><<<(unsigned)ntiles, kThreads, 0, s>>>(data, src, total_units, out, sums,
-                                                                 sc, status);
-    pl_tail_kernel<true><<<wgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
+    pl_units<kSum><<<unit_grid(resident_grid(pl_units<kSum>, occ_sum)), kThreads, 0, s>>>(
+        data, src, total_units, out, sums, sc, status);
+    pl_tail<true><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   } else {
-    pl_decode_kernel<false><<<(unsigned)ntiles, kThreads, 0, s>>>(data, src, total_units, out,
-                                                                  sums, sc, status);
-    pl_tail_kernel<false><<<wgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
+    pl_units<kStore><<<unit_grid(resident_grid(pl_units<kStore>, occ_store)), kThreads, 0, s>>>(
+        data, src, total_units, out, sums, sc, status);
+    pl_tail<false><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   }
   return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
 }

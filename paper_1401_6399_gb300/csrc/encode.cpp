@@ -260,10 +260,7 @@ int bp_index_encode(const uint32_t *values, const uint64_t *offs, uint32_t count
 }
 
 size_t bp_encode_bound(size_t n, int layout) {
-  if (layout == BP_LAYOUT_PAPER) {
-    const size_t nb = n / 128;
-    return bp_fmt::kPaperHeader + (nb / 16) * 16 + nb % 16 + nb * 512 + (n % 128) * 5;
-  }
+  if (layout == BP_LAYOUT_PAPER) return bp_fmt::pl_bound(n);
   if (layout == BP_LAYOUT_GPU) {
     const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(n);
     return g.off_payload + 512 * g.nblocks;

@@ -34,6 +34,13 @@ BP_HD GlGeometry gl_geometry(size_t n) {
   return g;
 }
 
+// Largest PL stream of n integers: every block at width 32 plus its width
+// byte, and five bytes per varint of the tail.
+BP_HD uint64_t pl_bound(uint64_t n) {
+  const uint64_t nb = n / 128;
+  return kPaperHeader + (nb / 16) * 16 + nb % 16 + nb * 512 + (n % 128) * 5;
+}
+
 // Work units of a list in a batch: GL -> groups of 32 blocks; PL -> one
 // unit per 128-integer block plus one for the varint tail.
 BP_HD uint64_t units_of(uint64_t n, int layout) {
