@@ -92,8 +92,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     const uint64_t q = u - base;
     if (q >= v.nsuper) continue;
     SuperInfo si;
-    if (gl_super(v, (uint32_t)q, lane, si, status))
+    if (gl_super(v, (uint32_t)q, lane, si, status)) {
+      // Pull the superblock's payload (contiguous, 16-byte aligned, a multiple
+      // of 16 bytes) into L2 with one bulk prefetch: the 32 blocks then
+      // load from L2 instead of paying one DRAM round trip each.
+      const uint32_t w0 = __shfl_sync(kFull, si.woff, 0);
+      const uint32_t w1 = __shfl_sync(kFull, si.woff + 4u * si.b, si.nblk - 1);
+      if (lane == 0 && w1 > w0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v.payload + w0),
+                     "r"(4u * (w1 - w0)) : "memory");
       gl_decode_unit<SUM>(v, si, (uint32_t)q, lane, out + out_off, acc);
+    }
   }
   if (SUM && cur != 0xFFFFFFFFu) flush_sum(acc, sums + cur, lane);
 }
