@@ -162,7 +162,7 @@ def encode_all(lists, layout: int):
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("common.cuh", "gl_block.cuh", "decode_gl.cu", "format.h", "decode.h"):
+    for f in ("common.cuh", "bulk.cuh", "gl_block.cuh", "decode_gl.cu", "format.h", "decode.h"):
         with open(os.path.join(ROOT, "paper_1401_6399_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -4,10 +4,12 @@
 // Work unit: a superblock of 32 blocks (4096 integers) per warp; a persistent
 // grid strides over the units of all lists.  Every block decodes on its own
 // from its skip header, so no carry crosses blocks (Section 4.3 container,
-// Algorithm 1 with the D4 prefix of Section 5 restarted per block).
+// Algorithm 1 with the D4 prefix of Section 5 restarted per block).  The
+// warp stages the superblock's payload in shared memory with one bulk copy
+// and decodes its 32 blocks from there.
 #include "decode.h"
+#include "bulk.cuh"
 #include "gl_block.cuh"
-
 
 namespace bp {
 
@@ -15,6 +17,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMinBlocks = 5;  // 40 resident warps per SM
+// Shared-memory stage per warp: a superblock whose payload fits (b <= 8 on
+// average) is brought in with one bulk copy; larger ones read global memory.
+constexpr uint32_t kStageBytes = 4096;
 
 
 // Store (or sum) one decoded block: lane l holds positions 16(l%8)+4t+l/8.
@@ -50,6 +55,22 @@ __device__ __forceinline__ void gl_decode_unit(const GlView &v, const SuperInfo 
   }
 }
 
+template <bool SUM>
+__device__ __forceinline__ void gl_decode_unit_smem(const GlView &v, const SuperInfo &si,
+                                                    uint32_t q, uint32_t w0, uint32_t sbase,
+                                                    int lane, uint32_t *__restrict__ out,
+                                                    uint64_t &acc) {
+  for (uint32_t j = 0; j < si.nblk; j++) {
+    const int b = (int)__shfl_sync(kFull, si.b, j);
+    const uint32_t F = __shfl_sync(kFull, si.F, j);
+    const uint32_t woff = __shfl_sync(kFull, si.woff, j);
+    const uint32_t blk = q * 32u + j;
+    uint32_t x[4];
+    gl_block_values_from(b, SharedWords{sbase + 4u * (woff - w0)}, F, lane, x);
+    store_block<SUM>(x, min(128u, v.n - 128u * blk), lane, out + 128ull * blk, acc);
+  }
+}
+
 __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane) {
 #pragma unroll
   for (int dd = 16; dd > 0; dd >>= 1) acc += __shfl_down_sync(kFull, acc, dd);
@@ -68,6 +89,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kThreads) >> 5;
+  __shared__ __align__(128) uint8_t s_stage[kThreads / 32][kStageBytes];
+  __shared__ __align__(8) uint64_t s_bar[kThreads / 32];
+  const int wl = threadIdx.x >> 5;
+  const uint32_t bar = smem_addr(&s_bar[wl]);
+  const uint32_t sbase = smem_addr(&s_stage[wl][0]);
+  uint32_t phase = 0;
+  if (lane == 0) bulk_bar_init(bar);
+  __syncwarp();
   uint32_t cur = 0xFFFFFFFFu;
   bool ok = false;
   GlView v;
@@ -93,14 +122,27 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     if (q >= v.nsuper) continue;
     SuperInfo si;
     if (gl_super(v, (uint32_t)q, lane, si, status)) {
-      // Pull the superblock's payload (contiguous, 16-byte aligned, a multiple
-      // of 16 bytes) into L2 with one bulk prefetch: the 32 blocks then
-      // load from L2 instead of paying one DRAM round trip each.
       const uint32_t w0 = __shfl_sync(kFull, si.woff, 0);
       const uint32_t w1 = __shfl_sync(kFull, si.woff + 4u * si.b, si.nblk - 1);
-      if (lane == 0 && w1 > w0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v.payload + w0),
-                     "r"(4u * (w1 - w0)) : "memory");
+      // The superblock's payload is contiguous, 16-byte aligned and a multiple
+      // of 16 bytes: one bulk copy stages it (or, if too large for the stage,
+      // one bulk prefetch pulls it into L2), so its 32 blocks cost one memory
+      // round trip instead of one each.
+      const uint32_t bytes = 4u * (w1 - w0);
+      if (bytes > 0 && bytes <= kStageBytes) {
+        if (lane == 0) bulk_load(bar, sbase, v.payload + w0, bytes);
+        const bool done = bulk_wait(bar, phase);
+        phase ^= 1u;
+        if (!__all_sync(kFull, done)) {  // give up: record it, let the copy land, stop
+          if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
+          bulk_wait(bar, phase ^ 1u);
+          return;
+        }
+        gl_decode_unit_smem<SUM>(v, si, (uint32_t)q, w0, sbase, lane, out + out_off, acc);
+        __syncwarp();
+        continue;
+      }
+      if (lane == 0 && bytes > 0) bulk_prefetch_l2(v.payload + w0, bytes);
       gl_decode_unit<SUM>(v, si, (uint32_t)q, lane, out + out_off, acc);
     }
   }

@@ -28,6 +28,7 @@
 //
 // Work unit u of a list: its block u - unit_base, then one unit for the tail.
 #include "decode.h"
+#include "bulk.cuh"
 #include "pl_block.cuh"
 
 namespace bp {
@@ -44,6 +45,7 @@ constexpr uint32_t kChunk = 32;     // work units per seed chunk
 constexpr uint32_t kScanPer = 16;   // chunks per thread in the chunk scan
 constexpr uint32_t kScanTile = kThreads * kScanPer;
 constexpr int kUnitMinBlocks = 5;  // resident CTAs per SM for pl_units (<= 51 registers)
+constexpr uint32_t kStageBytes = 4096;  // per warp of pl_units: a chunk's blocks at b <= 7
 constexpr uint64_t kOffMask = (1ull << 56) - 1;
 constexpr uint64_t kBadEntry = ~0ull;  // width byte 0xFF: no block to decode
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -603,6 +605,13 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
   const uint64_t warp = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kThreads) >> 5;
   const uint64_t nch = (total_units + kChunk - 1) / kChunk;
+  __shared__ __align__(128) uint8_t s_stage[kThreads / 32][kStageBytes];
+  __shared__ __align__(8) uint64_t s_bar[kThreads / 32];
+  const uint32_t bar = smem_addr(&s_bar[threadIdx.x >> 5]);
+  const uint32_t sbase = smem_addr(&s_stage[threadIdx.x >> 5][0]);
+  uint32_t phase = 0;
+  if (lane == 0) bulk_bar_init(bar);
+  __syncwarp();
   uint64_t acc = 0;
   uint32_t acc_list = kNone;
   for (uint64_t ch = warp; ch < nch; ch += nwarps) {
@@ -612,6 +621,35 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
     uint32_t li = src.find(u0);
     bp_list L = src.get(li);
     uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+    // The chunk's leading blocks of list li (lanes [0, m)) lie back to back in
+    // the meta-block region, 16-byte aligned, only width lines between them:
+    // stage them in shared memory with one bulk copy when they fit.
+    uint32_t staged = 0;
+    uint64_t st0 = 0;
+    {
+      const uint64_t k0 = u0 - L.unit_base, nb0 = L.n / 128u;
+      uint64_t m = nb0 > k0 ? nb0 - k0 : 0;
+      if (m > cnt) m = cnt;
+      if (m > nxt - u0) m = nxt - u0;
+      const uint64_t offl = eL & kOffMask;
+      const uint32_t bl = (uint32_t)(eL >> 56);
+      const bool fit = __all_sync(kFull, (uint32_t)lane >= m || (bl <= 32u && (offl & 15u) == 0));
+      if (m > 0 && fit) {
+        st0 = __shfl_sync(kFull, offl, 0);
+        const uint64_t bytes = __shfl_sync(kFull, offl + 16ull * bl, (int)m - 1) - st0;
+        if (bytes > 0 && bytes <= kStageBytes) {
+          if (lane == 0) bulk_load(bar, sbase, data + L.enc_offset + st0, (uint32_t)bytes);
+          const bool done = bulk_wait(bar, phase);
+          phase ^= 1u;
+          if (!__all_sync(kFull, done)) {  // give up: record it, let the copy land, stop
+            if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
+            bulk_wait(bar, phase ^ 1u);
+            return;
+          }
+          staged = (uint32_t)m;
+        }
+      }
+    }
     uint32_t carry = 0;
     if (MODE != kColsum) carry = comp(sc.chunk[ch], s);
     bool head = false;
@@ -638,7 +676,10 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
         continue;
       }
       uint32_t d[4];
-      pl_block_deltas((int)b, data + L.enc_offset + (e & kOffMask), lane, d);
+      if (j < staged)
+        pl_block_deltas_from((int)b, PlSharedWords{sbase + (uint32_t)((e & kOffMask) - st0)}, lane, d);
+      else
+        pl_block_deltas((int)b, data + L.enc_offset + (e & kOffMask), lane, d);
       if (MODE == kColsum) {
         carry += d[0] + d[1] + d[2] + d[3];
         continue;
@@ -670,6 +711,7 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
         o[12] = x3;
       }
     }
+    if (staged) __syncwarp();  // every lane is done with the stage before it is refilled
     if (MODE == kColsum) {
       carry += __shfl_xor_sync(kFull, carry, 1);
       carry += __shfl_xor_sync(kFull, carry, 2);

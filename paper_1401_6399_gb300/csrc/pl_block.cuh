@@ -22,9 +22,24 @@ __device__ __forceinline__ uint32_t pl_word(const uint8_t *blk, uint32_t i) {
   return __funnelshift_r(__ldg(p), __ldg(p + 1), 8u * m);
 }
 
-template <int B, bool ALIGNED>
-__device__ __forceinline__ void pl_lane_deltas(const uint8_t *__restrict__ blk, int lane,
-                                               uint32_t d[4]) {
+// Word i of a block in global memory (any byte alignment) or staged in
+// shared memory (16-byte aligned).
+template <bool ALIGNED>
+struct PlGlobalWords {
+  const uint8_t *blk;
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return pl_word<ALIGNED>(blk, i); }
+};
+struct PlSharedWords {
+  uint32_t base;  // shared-window address of the block
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(base + 4u * i));
+    return v;
+  }
+};
+
+template <int B, class L>
+__device__ __forceinline__ void pl_lane_deltas(const L &ld, int lane, uint32_t d[4]) {
   if constexpr (B == 0) {
     d[0] = d[1] = d[2] = d[3] = 0u;
   } else {
@@ -38,7 +53,7 @@ __device__ __forceinline__ void pl_lane_deltas(const uint8_t *__restrict__ blk, 
     uint32_t a[NW + 1];
 #pragma unroll
     for (int k = 0; k < NW; k++)
-      a[k] = (w0 + k < (uint32_t)B) ? pl_word<ALIGNED>(blk, 4u * (w0 + k) + s) : 0u;
+      a[k] = (w0 + k < (uint32_t)B) ? ld(4u * (w0 + k) + s) : 0u;
     a[NW] = 0u;
     uint32_t u[UW + 1];
 #pragma unroll
@@ -55,14 +70,12 @@ __device__ __forceinline__ void pl_lane_deltas(const uint8_t *__restrict__ blk, 
 
 // Runtime-width dispatch; b is warp-uniform.  Returns the 4 deltas of lane l
 // for block positions 16c + 4j + s.
-__device__ __forceinline__ void pl_block_deltas(int b, const uint8_t *__restrict__ blk,
-                                                int lane, uint32_t d[4]) {
-  const bool aligned = (reinterpret_cast<uintptr_t>(blk) & 3u) == 0;
+template <class L>
+__device__ __forceinline__ void pl_block_deltas_from(int b, const L &ld, int lane, uint32_t d[4]) {
   switch (b) {
-#define BP_CASE(B)                                                  \
-  case B:                                                           \
-    if (aligned) pl_lane_deltas<B, true>(blk, lane, d);             \
-    else pl_lane_deltas<B, false>(blk, lane, d);                    \
+#define BP_CASE(B)                       \
+  case B:                                \
+    pl_lane_deltas<B>(ld, lane, d);      \
     break;
     BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
     BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
@@ -73,6 +86,14 @@ __device__ __forceinline__ void pl_block_deltas(int b, const uint8_t *__restrict
     default:
       d[0] = d[1] = d[2] = d[3] = 0u;
   }
+}
+
+__device__ __forceinline__ void pl_block_deltas(int b, const uint8_t *__restrict__ blk,
+                                                int lane, uint32_t d[4]) {
+  if ((reinterpret_cast<uintptr_t>(blk) & 3u) == 0)
+    pl_block_deltas_from(b, PlGlobalWords<true>{blk}, lane, d);
+  else
+    pl_block_deltas_from(b, PlGlobalWords<false>{blk}, lane, d);
 }
 
 }  // namespace bp
