@@ -338,6 +338,63 @@ def pair_sweep(stream, reps: int):
     return out
 
 
+def pair_batch(stream, reps: int, pairs: int = 64):
+    """The pair sweep as independent pairs per launch: 64 longer lists of 2^22
+    uniform values of [0,2^26) (seeds 0x3100+i) and, per length ratio, 64
+    shorter lists sharing 10% of their values with their partner, all in one
+    resident index (together far larger than L2); one bp_query_batch of 64
+    two-term queries per launch."""
+    import torch
+    import workloads as W
+    from paper_1401_6399_gb300 import api, capi
+    ms = (1 << 22, 1 << 18, 1 << 14, 1 << 10, 1 << 8)
+    fv, fo = W.many("uniform", [1 << 22] * pairs, 0, 1 << 26, 0x3100)
+    parts, lens = [fv], [np.diff(fo).astype(np.uint64)]
+    for m in ms:
+        k = round(0.1 * m)
+        parts += [W.pair_short(fv[int(fo[i]):int(fo[i + 1])], m, k, 1 << 26, 0x3200 + 131 * i + m)
+                  for i in range(pairs)]
+        lens.append(np.full(pairs, m, np.uint64))
+    lens = np.concatenate(lens)
+    offs = np.zeros(lens.size + 1, np.uint64)
+    np.cumsum(lens, out=offs[1:])
+    idx = api.Index(np.concatenate(parts), offs)
+    del parts, fv
+    dev = "cuda"
+    out = {}
+    for j, m in enumerate(ms):
+        k = round(0.1 * m)
+        terms = np.empty(2 * pairs, np.uint32)
+        terms[0::2] = pairs * (j + 1) + np.arange(pairs)
+        terms[1::2] = np.arange(pairs)
+        toff = np.arange(0, 2 * pairs + 1, 2, dtype=np.uint64)
+        total = pairs * k
+        d_terms = torch.from_numpy(terms.view(np.int32).copy()).to(dev)
+        d_off = torch.from_numpy(toff.view(np.int64).copy()).to(dev)
+        res = torch.empty(total, dtype=torch.int32, device=dev)
+        out_off = torch.empty(pairs + 1, dtype=torch.int64, device=dev)
+        counts = torch.empty(pairs, dtype=torch.int32, device=dev)
+        sb = capi.bp_query_batch_scratch_bytes(idx.h_lists, terms, toff, total)
+        scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+
+        def call():
+            idx.query_batch_async(d_terms, d_off, pairs, terms.size, res, out_off, counts,
+                                  scratch, st, stream)
+        with torch.cuda.stream(stream):
+            call()
+        stream.synchronize()
+        assert int(st.item()) == 0
+        assert (counts.cpu().numpy() == k).all()  # exact by construction
+        ms_b = time_launches(stream, call, reps, 2)
+        out[f"m=2^{int(np.log2(m))}"] = {
+            "batch_us": round(1e3 * ms_b, 2), "us_per_pair": round(1e3 * ms_b / pairs, 3),
+            "pairs_per_s": round(pairs / (ms_b * 1e-3), 1),
+            "short_gints": round(pairs * m / (ms_b * 1e-3) / 1e9, 2)}
+        del scratch, res
+    return out
+
+
 def batched_queries(stream, reps: int, plain_queries: int):
     """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
     2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
@@ -603,6 +660,11 @@ def run_ours(args, rank, world, local):
             extra["pair_sweep"] = pair_sweep(stream, reps=20)
         except Exception as e:  # report, do not hide the headline
             extra["pair_sweep"] = {"error": repr(e)[:300]}
+        try:
+            extra["pair_batch_64"] = pair_batch(stream, reps=10)
+        except Exception as e:
+            extra["pair_batch_64"] = {"error": repr(e)[:300]}
+        torch.cuda.empty_cache()
         try:
             extra["batched_queries"] = batched_queries(stream, reps=5, plain_queries=2000)
         except Exception as e:

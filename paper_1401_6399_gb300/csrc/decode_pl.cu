@@ -653,6 +653,68 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
     uint32_t carry = 0;
     if (MODE != kColsum) carry = comp(sc.chunk[ch], s);
     bool head = false;
+    if (staged == kChunk) {
+      // Fast path: all 32 units are staged blocks of list li (no list change,
+      // no tail unit); each lane's block offset in the stage and width are
+      // packed into one word.
+      const uint64_t k0 = u0 - L.unit_base;
+      if (k0 == 0) {
+        carry = 0;
+        head = true;
+      }
+      const uint32_t pk = (uint32_t)((eL & kOffMask) - st0) | (uint32_t)((eL >> 56) << 16);
+      if (MODE == kColsum) {
+#pragma unroll 1
+        for (uint32_t j = 0; j < kChunk; j++) {
+          const uint32_t p = __shfl_sync(kFull, pk, j);
+          uint32_t d[4];
+          pl_block_deltas_from((int)(p >> 16), PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
+          carry += d[0] + d[1] + d[2] + d[3];
+        }
+        __syncwarp();  // every lane is done with the stage before it is refilled
+        carry += __shfl_xor_sync(kFull, carry, 1);
+        carry += __shfl_xor_sync(kFull, carry, 2);
+        carry += __shfl_xor_sync(kFull, carry, 4);
+        const uint32_t c1 = __shfl_sync(kFull, carry, 8), c2 = __shfl_sync(kFull, carry, 16),
+                       c3 = __shfl_sync(kFull, carry, 24);
+        if (lane == 0) {
+          sc.chunk[ch] = make_uint4(carry, c1, c2, c3);
+          sc.chunk_head[ch] = head ? 1u : 0u;
+        }
+        continue;
+      }
+      uint32_t *o = out + L.out_offset + 128ull * k0 + 16 * c + s;
+      if (MODE == kSum && acc_list != li) {
+        if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
+        acc_list = li;
+      }
+#pragma unroll 1
+      for (uint32_t j = 0; j < kChunk; j++) {
+        const uint32_t p = __shfl_sync(kFull, pk, j);
+        uint32_t d[4];
+        pl_block_deltas_from((int)(p >> 16), PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
+        uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
+        uint32_t inc = x3;
+#pragma unroll
+        for (int dd = 1; dd < 8; dd <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+          if (c >= dd) inc += t;
+        }
+        const uint32_t base = carry + inc - x3;
+        carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
+        if (MODE == kSum) {
+          acc += (uint64_t)(x0 + base) + (x1 + base) + (x2 + base) + (x3 + base);
+        } else {
+          o[0] = x0 + base;
+          o[4] = x1 + base;
+          o[8] = x2 + base;
+          o[12] = x3 + base;
+          o += 128;
+        }
+      }
+      __syncwarp();  // every lane is done with the stage before it is refilled
+      continue;
+    }
     for (uint32_t j = 0; j < cnt; j++) {
       const uint64_t u = u0 + j;
       if (u == nxt) {
