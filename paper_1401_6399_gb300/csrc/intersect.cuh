@@ -282,18 +282,23 @@ __device__ __forceinline__ void tile_emit(const uint32_t v[4], const bool hit[4]
   }
   if (lane == 0) s_wcnt[w] = tot;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < kIxWarps; i++) {
-      const uint32_t c = s_wcnt[i];
-      s_wcnt[i] = run;
-      run += c;
+  if (w == 0) {
+    const uint32_t c = lane < kIxWarps ? s_wcnt[lane] : 0u;
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < kIxWarps; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += y;
     }
-    const uint32_t P = lookback_exclusive(cp.state, t, run, to.status);
-    s_base[0] = P;
-    if (last_tile) {
-      *to.count = P + run;
-      if ((uint64_t)P + run > to.out_cap) set_status(to.status, BP_ERR_CAPACITY);
+    const uint32_t run = __shfl_sync(kFull, inc, kIxWarps - 1);
+    if (lane < kIxWarps) s_wcnt[lane] = inc - c;
+    const uint32_t P = lookback_exclusive_warp(cp.state, t, run, to.status, lane);
+    if (lane == 0) {
+      s_base[0] = P;
+      if (last_tile) {
+        *to.count = P + run;
+        if ((uint64_t)P + run > to.out_cap) set_status(to.status, BP_ERR_CAPACITY);
+      }
     }
   }
   __syncthreads();

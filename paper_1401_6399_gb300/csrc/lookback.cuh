@@ -25,31 +25,41 @@ __device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Called by one thread of tile t with the tile's own count; returns the
-// number of outputs of tiles 0..t-1.
-__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t *state, uint32_t t, uint32_t agg,
-                                                      uint32_t *status) {
+// Called by all 32 lanes of one warp of tile t with the tile's own count;
+// returns the number of outputs of tiles 0..t-1.  Each step inspects the 32
+// nearest tiles not yet accounted for (lane i: tile top - i), adds their
+// counts down to the nearest inclusive one and stops there, or moves 32
+// tiles back.
+__device__ __forceinline__ uint32_t lookback_exclusive_warp(uint64_t *state, uint32_t t,
+                                                           uint32_t agg, uint32_t *status,
+                                                           int lane) {
   if (t == 0) {
-    st_release_u64(state, (2ull << 32) | agg);
+    if (lane == 0) st_release_u64(state, (2ull << 32) | agg);
     return 0;
   }
-  st_release_u64(state + t, (1ull << 32) | agg);
+  if (lane == 0) st_release_u64(state + t, (1ull << 32) | agg);
   uint32_t excl = 0;
-  for (int64_t j = (int64_t)t - 1; j >= 0; j--) {
-    uint64_t s;
-    uint32_t spins = 0;
-    while (((s = ld_acquire_u64(state + j)) >> 32) == 0) {
-      if (++spins > kLookbackSpinLimit) break;
-      __nanosleep(64);
+  for (int64_t top = (int64_t)t - 1; top >= 0; top -= 32) {
+    const int64_t j = top - lane;
+    uint64_t s = 2ull << 32;  // before tile 0: an inclusive count of zero
+    if (j >= 0) {
+      uint32_t spins = 0;
+      while (((s = ld_acquire_u64(state + j)) >> 32) == 0) {
+        if (++spins > kLookbackSpinLimit) break;
+        __nanosleep(64);
+      }
     }
-    if ((s >> 32) == 0) {
-      set_status(status, BP_ERR_TIMEOUT);
+    const uint32_t flag = (uint32_t)(s >> 32);
+    if (__any_sync(kFull, flag == 0)) {
+      if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
       break;
     }
-    excl += (uint32_t)s;
-    if ((s >> 32) == 2) break;
+    const uint32_t incl = __ballot_sync(kFull, flag == 2);
+    const int stop = incl ? __ffs(incl) - 1 : 31;
+    excl += __reduce_add_sync(kFull, lane <= stop ? (uint32_t)s : 0u);
+    if (incl) break;
   }
-  st_release_u64(state + t, (2ull << 32) | (excl + agg));
+  if (lane == 0) st_release_u64(state + t, (2ull << 32) | (excl + agg));
   return excl;
 }
 
