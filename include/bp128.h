@@ -188,10 +188,16 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists,
  * (data_bytes) to d_data and of h_lists (count planned descriptors) to
  * d_lists, a reset of *d_status, the decode, and the copies of the decoded
  * lists (sum of n over the lists, as uint32) to h_out and of the status to
- * *h_status.  Host buffers should be pinned for the copies to be
- * asynchronous; all buffers belong to the caller and must stay alive until
- * the stream has passed the call.  Layout, scratch and errors as in
- * bp_decode_batch (sums are not offered here). */
+ * *h_status.  When the lists are laid out in order (streams and outputs
+ * ascending and disjoint, as bp_plan_lists plans them for packed buffers)
+ * and there are at least two, the copies and the decode run as a pipeline
+ * over groups of lists on the library's own streams, forked from `stream`
+ * and joined back into it (later work on `stream` still runs after the
+ * call); d_lists then holds per-group rebased descriptors afterwards.  Host
+ * buffers should be pinned for the copies to be asynchronous; all buffers
+ * belong to the caller and must stay alive until the stream has passed the
+ * call.  Layout, scratch and errors as in bp_decode_batch (sums are not
+ * offered here). */
 int bp_decode_batch_host(const uint8_t *h_data, size_t data_bytes,
                          const bp_list *h_lists, uint32_t count,
                          uint64_t total_units, int layout, uint8_t *d_data,

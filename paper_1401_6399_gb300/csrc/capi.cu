@@ -49,6 +49,133 @@ int decode_common(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, 
                               d_status, s);
 }
 
+// ---- bp_decode_batch_host as a pipeline over groups of lists ---------------------------------
+//
+// Copy-in of group g+1, decode of group g and copy-out of group g-1 overlap on
+// three library streams (the host link carries both directions at once);
+// they are forked from the caller's stream by an event and joined back into
+// it, so the call keeps the order of the work on that stream.
+
+constexpr int kPipeGroups = 8;
+constexpr int kNotPipelined = -1;
+
+struct HostPipe {
+  bool ready = false, failed = false;
+  cudaStream_t h2d = nullptr, dec = nullptr, d2h = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t in[kPipeGroups] = {}, decoded[kPipeGroups] = {};
+};
+
+std::mutex g_pipe_mu;
+
+// The device's pipeline resources, created once (g_pipe_mu held); nullptr
+// if they cannot be created.
+HostPipe *host_pipe() {
+  static HostPipe pipes[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  HostPipe &p = pipes[dev];
+  if (p.failed) return nullptr;
+  if (!p.ready) {
+    bool ok = cudaStreamCreateWithFlags(&p.h2d, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.dec, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.d2h, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming) == cudaSuccess;
+    for (int g = 0; ok && g < kPipeGroups; g++)
+      ok = cudaEventCreateWithFlags(&p.in[g], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&p.decoded[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      p.failed = true;
+      return nullptr;
+    }
+    p.ready = true;
+  }
+  return &p;
+}
+
+__global__ void rebase_units_kernel(bp_list *lists, uint32_t count, uint64_t base) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) lists[i].unit_base -= base;
+}
+
+// kNotPipelined unless the lists are laid out in order (streams and outputs
+// ascending and disjoint, units consecutive from 0) and there are at least two.
+int decode_host_pipelined(const uint8_t *h_data, const bp_list *h_lists, uint32_t count,
+                          uint64_t total_units, int layout, uint8_t *d_data, bp_list *d_lists,
+                          uint32_t *d_out, uint64_t out_cap, uint32_t *h_out, void *d_scratch,
+                          size_t scratch_bytes, uint32_t *d_status, uint32_t *h_status,
+                          cudaStream_t s) {
+  if (count < 2) return kNotPipelined;
+  uint64_t units = 0, total_n = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    const bp_list &L = h_lists[i];
+    if (L.unit_base != units || L.layout != (uint32_t)layout) return kNotPipelined;
+    if (i && (L.enc_offset < h_lists[i - 1].enc_offset + h_lists[i - 1].enc_bytes ||
+              L.out_offset < h_lists[i - 1].out_offset + h_lists[i - 1].n))
+      return kNotPipelined;
+    units += bp_fmt::units_of(L.n, layout);
+    total_n += L.n;
+  }
+  if (units != total_units) return kNotPipelined;
+  // groups of consecutive lists with about equal output
+  uint32_t first[kPipeGroups + 1];
+  int ng = 0;
+  {
+    uint64_t acc = 0;
+    first[ng++] = 0;
+    for (uint32_t i = 0; i + 1 < count && ng < kPipeGroups; i++) {
+      acc += h_lists[i].n;
+      if (acc * kPipeGroups >= total_n * (uint64_t)ng) first[ng++] = i + 1;
+    }
+    first[ng] = count;
+  }
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
+  HostPipe *p = host_pipe();
+  if (!p) return kNotPipelined;
+  int rc = BP_OK;
+  auto ck = [&rc](cudaError_t e) {
+    if (e != cudaSuccess && rc == BP_OK) rc = BP_ERR_CUDA;
+  };
+  ck(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s));
+  ck(cudaEventRecord(p->start, s));
+  ck(cudaStreamWaitEvent(p->h2d, p->start, 0));
+  ck(cudaMemcpyAsync(d_lists, h_lists, sizeof(bp_list) * count, cudaMemcpyHostToDevice, p->h2d));
+  for (int g = 0; g < ng; g++) {
+    const bp_list &A = h_lists[first[g]], &B = h_lists[first[g + 1] - 1];
+    const uint64_t lo = A.enc_offset, hi = B.enc_offset + B.enc_bytes;
+    ck(cudaMemcpyAsync(d_data + lo, h_data + lo, hi - lo, cudaMemcpyHostToDevice, p->h2d));
+    ck(cudaEventRecord(p->in[g], p->h2d));
+  }
+  for (int g = 0; g < ng; g++) {
+    const uint32_t a = first[g], cnt = first[g + 1] - a;
+    const bp_list &B = h_lists[first[g + 1] - 1];
+    const uint64_t ubase = h_lists[a].unit_base;
+    const uint64_t gunits = B.unit_base + bp_fmt::units_of(B.n, layout) - ubase;
+    ck(cudaStreamWaitEvent(p->dec, p->in[g], 0));
+    rebase_units_kernel<<<(cnt + 255) / 256, 256, 0, p->dec>>>(d_lists + a, cnt, ubase);
+    ck(cudaPeekAtLastError());
+    if (rc == BP_OK) {
+      const int r = bp_decode_batch(d_data, d_lists + a, cnt, gunits, layout, d_out, out_cap,
+                                    nullptr, d_scratch, scratch_bytes, d_status, p->dec);
+      if (r != BP_OK) rc = r;
+    }
+    ck(cudaEventRecord(p->decoded[g], p->dec));
+  }
+  for (int g = 0; g < ng; g++) {
+    const bp_list &A = h_lists[first[g]], &B = h_lists[first[g + 1] - 1];
+    const uint64_t lo = A.out_offset, hi = B.out_offset + B.n;
+    ck(cudaStreamWaitEvent(p->d2h, p->decoded[g], 0));
+    if (hi > lo)
+      ck(cudaMemcpyAsync(h_out + lo, d_out + lo, 4ull * (hi - lo), cudaMemcpyDeviceToHost, p->d2h));
+  }
+  // join: the caller's stream waits for everything above (also after an error)
+  ck(cudaEventRecord(p->done, p->d2h));
+  ck(cudaStreamWaitEvent(s, p->done, 0));
+  ck(cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -112,6 +239,10 @@ int bp_decode_batch_host(const uint8_t *h_data, size_t data_bytes, const bp_list
   }
   if (total_n > out_cap) return BP_ERR_CAPACITY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int piped = decode_host_pipelined(h_data, h_lists, count, total_units, layout, d_data,
+                                          d_lists, d_out, out_cap, h_out, d_scratch,
+                                          scratch_bytes, d_status, h_status, s);
+  if (piped != kNotPipelined) return piped;
   if (cudaMemcpyAsync(d_data, h_data, data_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(d_lists, h_lists, sizeof(bp_list) * count, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||

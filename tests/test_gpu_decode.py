@@ -130,6 +130,59 @@ def test_decode_batch(orc, layout):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_batch_host(orc, layout):
+    """bp_decode_batch_host from pinned host memory to pinned host memory.
+    Streams packed in list order take the pipelined path (groups of lists
+    copied in, decoded and copied out on library streams); streams packed in
+    reverse order take the one-shot path.  Both must give the oracle's lists,
+    and work enqueued afterwards on the caller's stream must see the output."""
+    rng = np.random.default_rng(7)
+    sizes = [0, 1, 130, 4096, 5000, 2048 * 16 + 3, 777, 128 * 33, 300000, 65536, 2, 1 << 20]
+    xs = [np.sort(rng.choice(1 << 31, n, replace=False)).astype(np.uint32) for n in sizes]
+    encs = [capi.bp_encode(x, layout) for x in xs]
+    ref = np.concatenate([oracle_decode(orc, x, layout) for x in xs])
+    total_n = ref.size
+    for order in ("ascending", "reversed"):
+        place = list(range(len(xs))) if order == "ascending" else list(reversed(range(len(xs))))
+        enc_off, pos = {}, 0
+        for i in place:
+            enc_off[i] = pos
+            pos += (encs[i].size + 15) // 16 * 16
+        host = np.zeros(max(pos, 16), np.uint8)
+        lists = np.zeros(len(xs), capi.BP_LIST)
+        out_off = 0
+        for i, (e, n) in enumerate(zip(encs, sizes)):
+            host[enc_off[i]:enc_off[i] + e.size] = e
+            lists[i] = (enc_off[i], e.size, out_off, 0, n, layout, 0)
+            out_off += n
+        total_units = capi.bp_plan_lists(lists)
+        h_data = torch.from_numpy(host).pin_memory()
+        h_lists = torch.from_numpy(lists.view(np.uint8).copy()).pin_memory()
+        h_out = torch.zeros(total_n, dtype=torch.int32).pin_memory()
+        h_status = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+        d_data = torch.empty(host.size, dtype=torch.uint8, device="cuda")
+        d_lists = torch.empty(h_lists.numel(), dtype=torch.uint8, device="cuda")
+        d_out = torch.empty(total_n, dtype=torch.int32, device="cuda")
+        d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        sb = capi.bp_decode_batch_scratch_bytes(lists)
+        scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device="cuda")
+        s = torch.cuda.Stream()
+        for _ in range(2):  # a second call reuses the library's streams and events
+            capi.check(capi.bp_decode_batch_host(
+                h_data.data_ptr(), host.size, h_lists.data_ptr(), len(xs), total_units, layout,
+                d_data.data_ptr(), d_lists.data_ptr(), d_out.data_ptr(), total_n,
+                h_out.data_ptr(), scratch.data_ptr(), sb, d_status.data_ptr(),
+                h_status.data_ptr(), s.cuda_stream), "bp_decode_batch_host")
+            with torch.cuda.stream(s):
+                after = d_out.clone()  # ordered after the call on the caller's stream
+            s.synchronize()
+            assert int(h_status.item()) == 0, order
+            assert np.array_equal(h_out.numpy().view(np.uint32), ref), order
+            assert np.array_equal(api.as_u32(after), ref), order
+            h_out.zero_()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
 def test_decode_full_size_batch(layout):
     """Four lists of 2^26 integers in [0, 2^29) (two uniform, two clustered),
     decoded in one batch launch as the benchmark does; a decoded list must be
