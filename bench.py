@@ -45,6 +45,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--lists", type=int, default=32)
+    p.add_argument("--layout", choices=["gpu", "paper"], default="gpu",
+                   help="stream layout of the timed decode (paper: the Section 4.3 layout)")
     p.add_argument("--log2n", type=int, default=26)
     p.add_argument("--no-extra", action="store_true", help="skip secondary measurements")
     p.add_argument("--no-e2e", action="store_true")
@@ -194,15 +196,16 @@ def load_peaks():
 
 # ---- the oracle as a CPU baseline --------------------------------------------------------
 
-def oracle_decode_rate(encs, ns, threads: int):
-    """Decode the given GL streams with the scalar oracle on `threads` host
-    threads; returns (Gint/s, seconds, threads)."""
+def oracle_decode_rate(encs, ns, threads: int, layout: int = 1):
+    """Decode the given streams (GL, or PL if layout is 0) with the scalar
+    oracle on `threads` host threads; returns (Gint/s, seconds, threads)."""
     from concurrent.futures import ThreadPoolExecutor
     from oracle import Oracle
     orc = Oracle()
+    dec = orc.gl_decode if layout == 1 else orc.pl_decode
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        outs = list(ex.map(lambda e: orc.gl_decode(e.tobytes()), encs))
+        outs = list(ex.map(lambda e: dec(e.tobytes()), encs))
     dt = time.perf_counter() - t0
     assert [o.size for o in outs] == list(ns)
     return sum(ns) / dt / 1e9, dt, threads
@@ -343,10 +346,10 @@ def pair_batch(stream, reps: int, pairs: int = 64):
     uniform values of [0,2^26) (seeds 0x3100+i) and, per length ratio, 64
     shorter lists sharing 10% of their values with their partner, all in one
     resident index (together far larger than L2); one bp_query_batch of 64
-    two-term queries per launch."""
+    two-term queries per launch, autotuned per length ratio."""
     import torch
     import workloads as W
-    from paper_1401_6399_gb300 import api, capi
+    from paper_1401_6399_gb300 import api, autotune, capi
     ms = (1 << 22, 1 << 18, 1 << 14, 1 << 10, 1 << 8)
     fv, fo = W.many("uniform", [1 << 22] * pairs, 0, 1 << 26, 0x3100)
     parts, lens = [fv], [np.diff(fo).astype(np.uint64)]
@@ -362,12 +365,14 @@ def pair_batch(stream, reps: int, pairs: int = 64):
     del parts, fv
     dev = "cuda"
     out = {}
+    saved = capi.bp_get_tuning()
     for j, m in enumerate(ms):
         k = round(0.1 * m)
         terms = np.empty(2 * pairs, np.uint32)
         terms[0::2] = pairs * (j + 1) + np.arange(pairs)
         terms[1::2] = np.arange(pairs)
         toff = np.arange(0, 2 * pairs + 1, 2, dtype=np.uint64)
+        tuned = autotune.tune_queries(idx, terms, toff, reps=2, save_cache=False)["best"]
         total = pairs * k
         d_terms = torch.from_numpy(terms.view(np.int32).copy()).to(dev)
         d_off = torch.from_numpy(toff.view(np.int64).copy()).to(dev)
@@ -390,8 +395,9 @@ def pair_batch(stream, reps: int, pairs: int = 64):
         out[f"m=2^{int(np.log2(m))}"] = {
             "batch_us": round(1e3 * ms_b, 2), "us_per_pair": round(1e3 * ms_b / pairs, 3),
             "pairs_per_s": round(pairs / (ms_b * 1e-3), 1),
-            "short_gints": round(pairs * m / (ms_b * 1e-3) / 1e9, 2)}
+            "short_gints": round(pairs * m / (ms_b * 1e-3) / 1e9, 2), "tuned": tuned}
         del scratch, res
+    capi.bp_set_tuning(**saved)
     return out
 
 
@@ -543,8 +549,12 @@ def run_ours(args, rank, world, local):
     L = args.lists
     seed = SEED_BASE + 4096 * rank
     lists = make_lists("uniform", L, n, UNIVERSE, seed)
-    encs = encode_all(lists, capi.BP_LAYOUT_GPU)
-    batch = api.ListBatch(encs, [n] * L, capi.BP_LAYOUT_GPU)
+    layout = capi.BP_LAYOUT_PAPER if args.layout == "paper" else capi.BP_LAYOUT_GPU
+    encs = encode_all(lists, layout)
+    batch = api.ListBatch(encs, [n] * L, layout)
+    # kernels of one bp_decode_batch call: GL one; PL plan, parse, resolve,
+    # emit, leftover, column sums, three scan kernels, decode, tail
+    launches_per_step = 1 if layout == capi.BP_LAYOUT_GPU else 11
     total_n = n * L
     out = torch.empty(total_n, dtype=torch.int32, device="cuda")
     status = api.status_tensor()
@@ -594,7 +604,7 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (ms_local * 1e-3) / 1e9
     sha = kernel_sha()
-    traffic = profiled_traffic(sha)
+    traffic = profiled_traffic(sha) if layout == capi.BP_LAYOUT_GPU else None
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -602,19 +612,22 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": f"decode {L} lists x 2^{args.log2n} uniform uint32 of [0,2^29) "
-                               "per GPU, S4-BP128-D4 GPU layout, one bp_decode_batch launch",
+                               f"per GPU, S4-BP128-D4 {'GPU' if layout else 'paper'} layout, "
+                               "one bp_decode_batch call",
                    "lists_per_gpu": L, "ints_per_list": n,
                    "compressed_bytes_per_gpu": comp_bytes,
                    "bits_per_int": round(8 * comp_bytes / total_n, 3),
                    "l2": "inputs (compressed) and outputs larger than L2; no flush",
                    "parallelism": f"weak x{world}"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "gl_decode_kernel<false>", "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel": "gl_decode_kernel<false>" if layout else
+                               "PL decode call (all its kernels)",
+                     "algorithmic_bytes_per_launch": alg_bytes,
                      "frac_of_nominal_8TBs": round(achieved / 8000.0, 4)},
     }
 
@@ -624,7 +637,7 @@ def run_ours(args, rank, world, local):
         # decode + sum (compressed bytes only)
         sums = torch.zeros(L, dtype=torch.int64, device="cuda")
         ms_sum = time_launches(stream, lambda: batch.sum_into(sums, status, stream), reps, 2)
-        extra["gl_decode_sum_uniform"] = {
+        extra[f"{'gl' if layout else 'pl'}_decode_sum_uniform"] = {
             "gints": round(total_n / (ms_sum * 1e-3) / 1e9, 2), "ms": round(ms_sum, 4),
             "gbs_compressed": round(comp_bytes / (ms_sum * 1e-3) / 1e9, 1)}
         # clustered lists
@@ -693,7 +706,7 @@ def run_ours(args, rank, world, local):
         def e2e_step():
             capi.check(capi.bp_decode_batch_host(
                 h_data.data_ptr(), h_data.numel(), h_lists.data_ptr(), L, batch.total_units,
-                capi.BP_LAYOUT_GPU, d_data.data_ptr(), d_lists.data_ptr(), out.data_ptr(),
+                layout, d_data.data_ptr(), d_lists.data_ptr(), out.data_ptr(),
                 total_n, h_out.data_ptr(), batch.scratch.data_ptr(), batch.scratch_bytes,
                 status.data_ptr(), h_status.data_ptr(), stream.cuda_stream), "e2e")
 
@@ -713,10 +726,11 @@ def run_ours(args, rank, world, local):
     if world == 1 and rank == 0 and not args.no_cpu:
         threads = min(16, os.cpu_count() or 1)
         k = min(L, 16)
-        val, dt, used = oracle_decode_rate(encs[:k], [n] * k, threads)
+        val, dt, used = oracle_decode_rate(encs[:k], [n] * k, threads, layout)
         result["cpu_baseline"] = {
             "value": round(val, 4), "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{k} of the {L} GL-encoded lists (2^{args.log2n} ints each) decoded by "
+            "sample": f"{k} of the {L} {'GL' if layout else 'PL'}-encoded lists "
+                      f"(2^{args.log2n} ints each) decoded by "
                       f"the scalar C oracle on {used} threads, {dt:.1f} s wall"}
     if rank == 0:
         print(json.dumps(result), flush=True)

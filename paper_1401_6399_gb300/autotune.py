@@ -46,9 +46,10 @@ def _time_ms(fn, reps: int, stream) -> float:
 
 
 def tune_queries(index, terms: np.ndarray, term_off: np.ndarray, reps: int = 3,
-                 space: dict | None = None) -> dict:
+                 space: dict | None = None, save_cache: bool = True) -> dict:
     """Tune bp_query_batch on a sample batch (terms, term_off) of `index`.
-    Returns {"best": params, "ms": {params: ms}} and installs the best."""
+    Returns {"best": params, "ms": {params: ms}} and installs the best (and
+    records it for this GPU unless save_cache is False)."""
     space = space or SPACE
     dev = index.device
     terms = np.ascontiguousarray(terms, np.uint32)
@@ -85,7 +86,8 @@ def tune_queries(index, terms: np.ndarray, term_off: np.ndarray, reps: int = 3,
     best = min(results, key=results.get)
     params = {"dense_blocks": best[0], "query_chunk_blocks": best[1], "query_warps": best[2]}
     capi.bp_set_tuning(**params)
-    save(params, results)
+    if save_cache:
+        save(params, results)
     return {"best": params, "ms": {f"{k[0]},{k[1]},{k[2]}": round(v, 4)
                                    for k, v in results.items()}}
 

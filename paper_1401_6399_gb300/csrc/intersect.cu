@@ -2,10 +2,12 @@
 // lists (Section 6; the result is output-to-input safe in the paper's sense
 // because each output value comes from the shorter list, in order).
 //
-//  fused (both GL): the shorter list r is decoded block by block in
-//      registers; candidate blocks of the longer list f are located through
-//      f's skip headers and decoded into shared memory only where needed;
-//      nothing decoded is written back to HBM.
+//  fused (both GL): each warp decodes a run of up to 8 blocks of the
+//      shorter list r into shared memory; candidate blocks of the longer
+//      list f are located through f's skip headers and decoded into a
+//      shared-memory window that moves forward with r's values (or probed
+//      one by one for very skewed pairs); nothing decoded is written back
+//      to HBM.
 //  unfused (any layout): both lists are decoded into scratch, then the
 //      decoded arrays are intersected by the same warp-level regimes.
 // Output: ballot/popc inside warps, a CTA scan, and a decoupled look-back
@@ -27,43 +29,85 @@ struct PairArgs {
   uint32_t nf;
 };
 
-// vpw: values of the shorter list per warp (8..128, a power of two).  Warps
-// that share an r block each decode it and take their slice.
+// Shared memory per warp: up to 8 decoded blocks of r (survivors compacted
+// in place), then the dense window of f.
+constexpr int kPairGroups = 8;
+constexpr int kPairWarpWords = kPairGroups * 128 + kIxDenseMax * 128;
+
+// vpw: values of the shorter list per warp, a power of two: 8..128 (a slice
+// of one block, for very skewed pairs) or 128 g for g = 2..8 blocks, which
+// the warp filters run by run with its window of f moving forward.
 __global__ void __launch_bounds__(kIxThreads)
     fused_pair_kernel(PairArgs a, Compaction cp, TileOut to, uint32_t ntiles, uint32_t dense_max,
                       uint32_t vpw) {
-  __shared__ uint32_t s_r[kIxWarps][128];
-  __shared__ uint32_t s_f[kIxWarps][kIxDenseMax * 128];
+  extern __shared__ uint32_t smem[];
   __shared__ uint32_t s_wcnt[kIxWarps], s_base[1], s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(cp.ticket, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t *s_r = smem + w * kPairWarpWords;
+  uint32_t *s_f = s_r + kPairGroups * 128;
 
   GlView R, F;
   const bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
   const bool okF = gl_view(a.f_enc, a.f_bytes, F) && F.n == a.nf;
   if ((!okR || !okF) && threadIdx.x == 0 && t == 0) set_status(to.status, BP_ERR_CORRUPT);
 
-  uint32_t v[4] = {0, 0, 0, 0};
-  bool valid[4] = {false, false, false, false}, hit[4] = {false, false, false, false};
+  uint32_t scount = 0;
   const uint64_t p0 = ((uint64_t)t * kIxWarps + w) * vpw;  // first r position of this warp
   if (okR && okF && p0 < a.nr) {
-    const uint32_t kb = (uint32_t)(p0 >> 7), s0 = (uint32_t)(p0 & 127u);
-    const uint32_t cnt = gl_block_into(R, kb, s_r[w], lane, to.status);
-    __syncwarp();
-    const uint32_t end = min(cnt, s0 + vpw);
+    const uint64_t p1 = min((uint64_t)a.nr, p0 + vpw);       // one past the last
+    const uint32_t kb0 = (uint32_t)(p0 >> 7), ng = (uint32_t)(((p1 - 1) >> 7) - kb0 + 1);
+    // bit 4g+j of `alive`: value 32j + lane of block kb0+g is in the range
+    uint32_t alive = 0;
+    for (uint32_t g = 0; g < ng; g++) {
+      const uint32_t cnt = gl_block_into(R, kb0 + g, s_r + 128u * g, lane, to.status);
+      const uint64_t bstart = 128ull * (kb0 + g);
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t pos = s0 + 32u * k + lane;
-      valid[k] = pos < end;
-      v[k] = valid[k] ? s_r[w][pos] : 0u;
+      for (int j = 0; j < 4; j++) {
+        const uint64_t pos = bstart + 32 * j + lane;
+        if (pos >= p0 && pos < p1 && (uint32_t)(32 * j + lane) < cnt) alive |= 1u << (4 * g + j);
+      }
     }
-    if (end > s0)
-      gl_membership(F, v, valid, hit, s_r[w][s0], s_r[w][end - 1], s_f[w], lane, dense_max,
-                    to.status);
+    __syncwarp();
+    FWin win = fwin_empty();
+    for (uint32_t g = 0; g < ng; g++) {
+      uint32_t v[4];
+      bool valid[4], hit[4];
+      uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        valid[j] = (alive >> (4 * g + j)) & 1u;
+        v[j] = s_r[128u * g + 32 * j + lane];
+        if (valid[j]) {
+          lo = min(lo, v[j]);
+          hi = max(hi, v[j]);
+        }
+      }
+      if (!__any_sync(kFull, (alive >> (4 * g)) & 0xFu)) continue;
+      lo = __reduce_min_sync(kFull, lo);
+      hi = __reduce_max_sync(kFull, hi);
+      gl_membership_win(F, v, valid, hit, lo, hi, s_f, win, lane, dense_max, to.status);
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (valid[j] && !hit[j]) alive &= ~(1u << (4 * g + j));
+    }
+    // compact the survivors, in order, to the front of s_r
+    for (uint32_t g = 0; g < ng; g++) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const bool a = (alive >> (4 * g + j)) & 1u;
+        const uint32_t x = s_r[128u * g + 32 * j + lane];
+        const uint32_t m = __ballot_sync(kFull, a);
+        __syncwarp();
+        if (a) s_r[scount + __popc(m & lanemask_lt())] = x;
+        scount += __popc(m);
+        __syncwarp();
+      }
+    }
   }
-  tile_emit(v, hit, t, t == ntiles - 1, cp, to, s_wcnt, s_base);
+  tile_emit_buf(s_r, scount, t, t == ntiles - 1, cp, to, s_wcnt, s_base);
 }
 
 __global__ void __launch_bounds__(kIxThreads)
@@ -98,17 +142,26 @@ uint32_t pair_tiles(uint64_t nr, uint32_t vpw = 128) {
   return (uint32_t)std::max<uint64_t>(1, (chunks + kIxWarps - 1) / kIxWarps);
 }
 
-// Values of the shorter list per warp: 128, unless the lists are so skewed
-// that every value probes a block of its own (ratio >= 128) and there are
-// too few values to fill the GPU -- then down to 8 (more warps, fewer
-// probes each).
+// Values of the shorter list per warp.  Very skewed pairs (every value
+// probes a block of its own, ratio >= 128) with too few values to fill the
+// GPU: down to 8 (more warps, fewer probes each).  Otherwise runs of up to 8
+// blocks per warp, as many as keep 16 warps per SM busy.
 uint32_t pair_vpw(uint64_t nr, uint64_t nf) {
-  if (nr == 0 || nf < 128 * nr) return 128;
-  const uint64_t want_warps = 16ull * device_sm_count() * 8;
-  uint32_t vpw = 128;
-  while (vpw > 8 && (nr + vpw - 1) / vpw < want_warps) vpw >>= 1;
-  return vpw;
+  if (nr == 0) return 128;
+  if (nf >= 128 * nr) {
+    const uint64_t want_warps = 16ull * device_sm_count() * 8;
+    uint32_t vpw = 128;
+    while (vpw > 8 && (nr + vpw - 1) / vpw < want_warps) vpw >>= 1;
+    return vpw;
+  }
+  const uint64_t want_warps = 16ull * device_sm_count();
+  uint32_t g = kPairGroups;
+  while (g > 1 && (nr + 128ull * g - 1) / (128ull * g) < want_warps) g >>= 1;
+  return 128u * g;
 }
+
+int g_pair_smem_set = 0;
+constexpr size_t kPairSmem = sizeof(uint32_t) * kPairWarpWords * kIxWarps;
 
 }  // namespace
 
@@ -140,8 +193,14 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
   if (mode == BP_MODE_FUSED) {
     const uint32_t vpw = pair_vpw(a.nr, a.nf);
     const uint32_t ft = pair_tiles(a.nr, vpw);
+    if (!g_pair_smem_set) {
+      if (cudaFuncSetAttribute(fused_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kPairSmem) != cudaSuccess)
+        return BP_ERR_CUDA;
+      g_pair_smem_set = 1;
+    }
     if (cudaMemsetAsync(sp, 0, compaction_bytes(ft), s) != cudaSuccess) return BP_ERR_CUDA;
-    fused_pair_kernel<<<ft, kIxThreads, 0, s>>>(
+    fused_pair_kernel<<<ft, kIxThreads, kPairSmem, s>>>(
         a, cp, to, ft, std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw);
     return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
   }

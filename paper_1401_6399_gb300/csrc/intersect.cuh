@@ -261,6 +261,104 @@ __device__ __forceinline__ void raw_membership(const uint32_t *__restrict__ f, u
   for (int k = 0; k < 4; k++) hit[k] = valid[k] && gmem_contains(f, lo, hi, v[k]);
 }
 
+// Decoded blocks [lo, hi] of f held in a warp's shared-memory window (none
+// if hi < lo).  A warp that filters increasing runs of values through the
+// same f keeps the window from one run to the next: runs of similar density
+// move it forward a block or two at a time.
+struct FWin {
+  int64_t lo, hi;
+  uint32_t len;       // decoded values in the window
+  uint32_t first_lo;  // f.first[lo]
+};
+
+__device__ __forceinline__ FWin fwin_empty() {
+  FWin w;
+  w.lo = 0;
+  w.hi = -1;
+  w.len = 0;
+  w.first_lo = 0;
+  return w;
+}
+
+// Largest k in [h, n) with a[k] <= v, given a[h] <= v: one probe of the 32
+// entries from h, then the 32-way search beyond them.
+__device__ __forceinline__ int64_t fwd_ubound(const uint32_t *__restrict__ a, uint64_t n,
+                                              uint32_t v, int64_t h, int lane) {
+  const uint64_t p = (uint64_t)h + lane;
+  const bool le = p < n && __ldg(a + p) <= v;
+  const uint32_t c = __popc(__ballot_sync(kFull, le));
+  if (c < 32u) return h + (int64_t)c - 1;
+  const uint64_t base = (uint64_t)h + 32;
+  return (int64_t)base + warp_ubound(a + base, n - base, v, lane);
+}
+
+// As gl_membership (dense or sparse by the span of f's blocks that can hold
+// [rmin, rmax]), with the dense blocks kept in `win` over `smem`
+// (kIxDenseMax * 128 words of this warp) for the next call: blocks already
+// decoded are not decoded again, and the block range is found by probing
+// forward from the window.  Runs must come in increasing order of values.
+__device__ __forceinline__ void gl_membership_win(const GlView &f, const uint32_t v[4],
+                                                  const bool valid[4], bool hit[4], uint32_t rmin,
+                                                  uint32_t rmax, uint32_t *smem, FWin &win,
+                                                  int lane, uint32_t dense_max, uint32_t *status) {
+#pragma unroll
+  for (int k = 0; k < 4; k++) hit[k] = false;
+  if (f.nblocks == 0) return;
+  const bool have = win.hi >= win.lo;
+  int64_t klo = (have && win.first_lo <= rmin) ? fwd_ubound(f.first, f.nblocks, rmin, win.lo, lane)
+                                              : warp_ubound(f.first, f.nblocks, rmin, lane);
+  int64_t khi;
+  if (klo >= 0) {
+    khi = fwd_ubound(f.first, f.nblocks, rmax, klo, lane);
+  } else {
+    khi = warp_ubound(f.first, f.nblocks, rmax, lane);
+    if (khi < 0) return;  // every value is below f's first value
+    klo = 0;
+  }
+  if (!(have && klo >= win.lo && khi <= win.hi)) {
+    const uint64_t span = (uint64_t)(khi - klo + 1);
+    if (span > dense_max) {  // sparse: every value looks up its own candidate block
+      int64_t cb[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        cb[k] = valid[k] ? lane_ubound(f.first, klo, khi, v[k]) : klo - 1;
+      lookup_probes(f, v, valid, cb, klo, hit, lane, status);
+      return;
+    }
+    // refill the window with blocks [klo, khi]; blocks it already holds move
+    // to the front instead of being decoded again
+    uint32_t keep = 0;
+    if (have && klo >= win.lo && klo <= win.hi) {
+      keep = (uint32_t)((win.hi < khi ? win.hi : khi) - klo + 1);
+      const uint32_t from = 128u * (uint32_t)(klo - win.lo), words = 128u * keep;
+      if (from) {
+        for (uint32_t i0 = 0; i0 < words; i0 += 32) {
+          const uint32_t i = i0 + lane;
+          const uint32_t x = i < words ? smem[from + i] : 0u;
+          __syncwarp();
+          if (i < words) smem[i] = x;
+          __syncwarp();
+        }
+      }
+    }
+    uint32_t len = 128u * keep;
+    if (keep && (uint64_t)klo + keep == f.nblocks) len = 128u * (keep - 1) + (f.n - 128u * (f.nblocks - 1));
+    for (uint32_t i = keep; i < (uint32_t)span; i++) {
+      const uint32_t c = gl_block_into(f, (uint32_t)klo + i, smem + 128u * i, lane, status);
+      len = 128u * i + c;
+      if (c < 128u) break;  // only the last block of f is short
+    }
+    __syncwarp();
+    win.lo = klo;
+    win.hi = khi;
+    win.len = len;
+    win.first_lo = __ldg(f.first + klo);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) hit[k] = valid[k] && smem_contains(smem, win.len, v[k]);
+  __syncwarp();
+}
+
 // Ordered output of one tile (all threads of the CTA call it).  Lane holds
 // positions 32k + lane of its warp's chunk; chunks are in warp order.
 struct TileOut {
@@ -270,17 +368,13 @@ struct TileOut {
   uint32_t *status;
 };
 
-__device__ __forceinline__ void tile_emit(const uint32_t v[4], const bool hit[4], uint32_t t,
-                                          bool last_tile, const Compaction &cp, const TileOut &to,
-                                          uint32_t *s_wcnt, uint32_t *s_base) {
+// Output position of warp w's first value in tile t, given each warp's count
+// (all threads of the CTA call it; warp 0 does the scan and the look-back).
+__device__ __forceinline__ uint64_t tile_base(uint32_t count, uint32_t t, bool last_tile,
+                                              const Compaction &cp, const TileOut &to,
+                                              uint32_t *s_wcnt, uint32_t *s_base) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t m[4], tot = 0;
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    m[k] = __ballot_sync(kFull, hit[k]);
-    tot += __popc(m[k]);
-  }
-  if (lane == 0) s_wcnt[w] = tot;
+  if (lane == 0) s_wcnt[w] = count;
   __syncthreads();
   if (w == 0) {
     const uint32_t c = lane < kIxWarps ? s_wcnt[lane] : 0u;
@@ -302,7 +396,19 @@ __device__ __forceinline__ void tile_emit(const uint32_t v[4], const bool hit[4]
     }
   }
   __syncthreads();
-  uint64_t pos = (uint64_t)s_base[0] + s_wcnt[w];
+  return (uint64_t)s_base[0] + s_wcnt[w];
+}
+
+__device__ __forceinline__ void tile_emit(const uint32_t v[4], const bool hit[4], uint32_t t,
+                                          bool last_tile, const Compaction &cp, const TileOut &to,
+                                          uint32_t *s_wcnt, uint32_t *s_base) {
+  uint32_t m[4], tot = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    m[k] = __ballot_sync(kFull, hit[k]);
+    tot += __popc(m[k]);
+  }
+  uint64_t pos = tile_base(tot, t, last_tile, cp, to, s_wcnt, s_base);
 #pragma unroll
   for (int k = 0; k < 4; k++) {
     if (hit[k]) {
@@ -311,6 +417,17 @@ __device__ __forceinline__ void tile_emit(const uint32_t v[4], const bool hit[4]
     }
     pos += __popc(m[k]);
   }
+}
+
+// Same for a warp whose `count` outputs are already compacted, in order, in
+// its shared buffer `buf`.
+__device__ __forceinline__ void tile_emit_buf(const uint32_t *buf, uint32_t count, uint32_t t,
+                                              bool last_tile, const Compaction &cp,
+                                              const TileOut &to, uint32_t *s_wcnt,
+                                              uint32_t *s_base) {
+  const uint64_t pos = tile_base(count, t, last_tile, cp, to, s_wcnt, s_base);
+  for (uint32_t i = threadIdx.x & 31; i < count; i += 32)
+    if (pos + i < to.out_cap) to.out[pos + i] = buf[i];
 }
 
 }  // namespace bp

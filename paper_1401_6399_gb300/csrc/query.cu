@@ -6,9 +6,11 @@
 //     items of `chunk` blocks.
 //  2. scan of the item counts.
 //  3. q_main: a persistent grid; every warp takes the next item from a device
-//     counter, decodes the item's blocks of the shortest list, and filters
-//     their values through the other lists in order (gl_membership: skip-
-//     header search, candidate blocks decoded into shared memory, never to
+//     counter, decodes the item's blocks of the shortest list into shared
+//     memory, and filters their values through the other lists in order,
+//     one list at a time and one block-sized run at a time
+//     (gl_membership_win: skip-header search, candidate blocks decoded into
+//     a shared-memory window that moves forward with the runs, never to
 //     HBM), then appends the survivors to an arena slot.
 //  4. q_count / scan / q_gather: per-query counts and the survivors copied in
 //     query and item order into the caller's output.
@@ -30,7 +32,9 @@ namespace {
 
 constexpr int kMaxTerms = 64;
 constexpr int kMaxChunk = 8;
-constexpr int kWarpSmemWords = 128 + kIxDenseMax * 128 + kMaxChunk * 128;
+// per warp: the item's decoded blocks (survivors are compacted in place),
+// then the dense window of the list being searched
+constexpr int kWarpSmemWords = kMaxChunk * 128 + kIxDenseMax * 128;
 
 inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -181,8 +185,7 @@ __global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *_
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t *s_r = smem + w * kWarpSmemWords;
-  uint32_t *s_f = s_r + 128;
-  uint32_t *s_stage = s_f + kIxDenseMax * 128;
+  uint32_t *s_f = s_r + kMaxChunk * 128;
   const uint32_t total = sc.base[nq];
   if (total > max_items) {  // the caller's scratch holds fewer work items
     if (threadIdx.x == 0 && blockIdx.x == 0) set_status(status, BP_ERR_SCRATCH);
@@ -201,47 +204,61 @@ __global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *_
     GlView V1;
     uint32_t scount = 0;
     if (term_view(data, lists, sc.sorted[tb], V1)) {
+      // the item's blocks of the shortest list; bit 4g+j of `alive`: value
+      // 32j + lane of block g is still a candidate
       const uint32_t b0 = c * chunk, b1 = min(V1.nblocks, b0 + chunk);
-      for (uint32_t blk = b0; blk < b1; blk++) {
-        const uint32_t cnt = gl_block_into(V1, blk, s_r, lane, status);
-        __syncwarp();
-        uint32_t v[4];
-        bool valid[4], hit[4];
+      const uint32_t ng = b1 > b0 ? b1 - b0 : 0u;
+      uint32_t alive = 0;
+      for (uint32_t g = 0; g < ng; g++) {
+        const uint32_t cnt = gl_block_into(V1, b0 + g, s_r + 128u * g, lane, status);
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-          valid[j] = (uint32_t)(32 * j + lane) < cnt;
-          v[j] = valid[j] ? s_r[32 * j + lane] : 0u;
+        for (int j = 0; j < 4; j++)
+          if ((uint32_t)(32 * j + lane) < cnt) alive |= 1u << (4 * g + j);
+      }
+      __syncwarp();
+      // Set-vs-Set: the candidates go through the other lists in order, each
+      // list searched run by run with its dense window moving forward
+      for (uint32_t t = 1; t < k && __any_sync(kFull, alive != 0u); t++) {
+        GlView F;
+        if (!term_view(data, lists, sc.sorted[tb + t], F)) {
+          if (lane == 0) set_status(status, BP_ERR_CORRUPT);
+          alive = 0;
+          break;
         }
-        __syncwarp();
-        for (uint32_t t = 1; t < k; t++) {
+        FWin win = fwin_empty();
+        for (uint32_t g = 0; g < ng; g++) {
+          uint32_t v[4];
+          bool valid[4], hit[4];
           uint32_t lo = 0xFFFFFFFFu, hi = 0u;
-          bool any = false;
 #pragma unroll
-          for (int j = 0; j < 4; j++)
+          for (int j = 0; j < 4; j++) {
+            valid[j] = (alive >> (4 * g + j)) & 1u;
+            v[j] = s_r[128u * g + 32 * j + lane];
             if (valid[j]) {
               lo = min(lo, v[j]);
               hi = max(hi, v[j]);
-              any = true;
             }
-          if (!__any_sync(kFull, any)) break;
+          }
+          if (!__any_sync(kFull, (alive >> (4 * g)) & 0xFu)) continue;
           lo = __reduce_min_sync(kFull, lo);
           hi = __reduce_max_sync(kFull, hi);
-          GlView F;
-          if (!term_view(data, lists, sc.sorted[tb + t], F)) {
-            if (lane == 0) set_status(status, BP_ERR_CORRUPT);
+          gl_membership_win(F, v, valid, hit, lo, hi, s_f, win, lane, dense_max, status);
 #pragma unroll
-            for (int j = 0; j < 4; j++) valid[j] = false;
-            break;
-          }
-          gl_membership(F, v, valid, hit, lo, hi, s_f, lane, dense_max, status);
-#pragma unroll
-          for (int j = 0; j < 4; j++) valid[j] = valid[j] && hit[j];
+          for (int j = 0; j < 4; j++)
+            if (valid[j] && !hit[j]) alive &= ~(1u << (4 * g + j));
         }
+      }
+      // compact the survivors, in order, to the front of s_r
+      for (uint32_t g = 0; g < ng; g++) {
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-          const uint32_t m = __ballot_sync(kFull, valid[j]);
-          if (valid[j]) s_stage[scount + __popc(m & lanemask_lt())] = v[j];
+          const bool a = (alive >> (4 * g + j)) & 1u;
+          const uint32_t x = s_r[128u * g + 32 * j + lane];
+          const uint32_t m = __ballot_sync(kFull, a);
+          __syncwarp();
+          if (a) s_r[scount + __popc(m & lanemask_lt())] = x;
           scount += __popc(m);
+          __syncwarp();
         }
       }
     } else if (lane == 0) {
@@ -254,7 +271,7 @@ __global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *_
     const bool fits = off + scount <= arena_cap;
     if (!fits && lane == 0) set_status(status, BP_ERR_CAPACITY);
     if (fits)
-      for (uint32_t i = lane; i < scount; i += 32) sc.arena[off + i] = s_stage[i];
+      for (uint32_t i = lane; i < scount; i += 32) sc.arena[off + i] = s_r[i];
     if (lane == 0) {
       sc.item_q[item] = q;
       sc.item_off[item] = fits ? off : ~0ull;
