@@ -509,6 +509,11 @@ def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
     srv = api.Server(idx, slots=4, max_batch_queries=8192, max_terms=8, slot_bytes=1 << 30,
                      deliver_answers=False)
     try:
+        # warm-up replay (not measured): lazy setup of the engine's streams
+        wt, wo = W.queries(lens, 2000, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x50FF)
+        srv.replay(np.arange(2000, dtype=np.uint64), wt, wo, W.poisson_arrivals(1e4, 2000, 0x51FF))
+        srv.drain(600.0)
+        srv.poll(with_answers=False)
         for rate in rates:
             n = int(min(300_000, rate * 5))
             terms, toff = W.queries(lens, n, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5000 + int(rate))
