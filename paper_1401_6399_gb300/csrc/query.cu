@@ -178,7 +178,10 @@ __device__ __forceinline__ bool term_view(const uint8_t *data, const bp_list *li
   return gl_view(data + L.enc_offset, L.enc_bytes, v) && v.n == L.n;
 }
 
-__global__ void q_main_kernel(const uint8_t *__restrict__ data, const bp_list *__restrict__ lists,
+// At most 80 registers: 3 CTAs of 8 warps (or 6 of 4) per SM; more warps
+// in flight matter more here than the few values it would keep in registers.
+__global__ void __launch_bounds__(256, 3)
+    q_main_kernel(const uint8_t *__restrict__ data, const bp_list *__restrict__ lists,
                               const uint64_t *__restrict__ toff, uint32_t nq, QScratch sc,
                               uint32_t max_items, uint64_t arena_cap, uint32_t chunk,
                               uint32_t dense_max, uint32_t *status) {
