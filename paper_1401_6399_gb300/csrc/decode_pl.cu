@@ -594,6 +594,72 @@ __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane
   acc = 0;
 }
 
+// Blocks j .. j+run-1 of a fully staged chunk, all of width B (pk of lane
+// u: the block's offset in the stage | width << 16).  Column sums, or the
+// decode with the running seed `carry`, stored through `o` or summed into acc.
+template <int B, int MODE>
+__device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run, uint32_t sbase,
+                                           int lane, uint32_t &carry, uint32_t *&o,
+                                           uint64_t &acc) {
+  const int c = lane & 7;
+#pragma unroll 1
+  for (uint32_t r = 0; r < run; r++) {
+    const uint32_t p = __shfl_sync(kFull, pk, j + r);
+    uint32_t d[4];
+    pl_lane_deltas<B>(PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
+    if (MODE == kColsum) {
+      carry += d[0] + d[1] + d[2] + d[3];
+      continue;
+    }
+    const uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
+    uint32_t inc = x3;
+#pragma unroll
+    for (int dd = 1; dd < 8; dd <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+      if (c >= dd) inc += t;
+    }
+    const uint32_t base = carry + inc - x3;
+    carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
+    if (MODE == kSum) {
+      acc += (uint64_t)(x0 + base) + (x1 + base) + (x2 + base) + (x3 + base);
+    } else {
+      o[0] = x0 + base;
+      o[4] = x1 + base;
+      o[8] = x2 + base;
+      o[12] = x3 + base;
+      o += 128;
+    }
+  }
+}
+
+// The 32 blocks of a fully staged chunk, one width dispatch per run of
+// consecutive blocks of equal width.
+template <int MODE>
+__device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int lane,
+                                             uint32_t &carry, uint32_t *o, uint64_t &acc) {
+  const uint32_t bw = pk >> 16;
+  for (uint32_t j = 0; j < kChunk;) {
+    const uint32_t b = __shfl_sync(kFull, bw, j);
+    const uint32_t same = __ballot_sync(kFull, bw == b) >> j;  // bit r: block j + r
+    const uint32_t run = ~same ? (uint32_t)__ffs(~same) - 1 : kChunk - j;
+    switch (b) {
+#define BP_CASE(B)                                                      \
+  case B:                                                               \
+    staged_run<B, MODE>(pk, j, run, sbase, lane, carry, o, acc);        \
+    break;
+      BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
+      BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
+      BP_CASE(14) BP_CASE(15) BP_CASE(16) BP_CASE(17) BP_CASE(18) BP_CASE(19) BP_CASE(20)
+      BP_CASE(21) BP_CASE(22) BP_CASE(23) BP_CASE(24) BP_CASE(25) BP_CASE(26) BP_CASE(27)
+      BP_CASE(28) BP_CASE(29) BP_CASE(30) BP_CASE(31) BP_CASE(32)
+#undef BP_CASE
+      default:
+        break;
+    }
+    j += run;
+  }
+}
+
 // Lane l = 8s + c owns column s, rows 4c..4c+3 of each block (positions
 // 16c + 4j + s); `carry` is the running D4 seed of its column.
 template <int MODE>
@@ -663,15 +729,15 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
         head = true;
       }
       const uint32_t pk = (uint32_t)((eL & kOffMask) - st0) | (uint32_t)((eL >> 56) << 16);
+      if (MODE == kSum && acc_list != li) {
+        if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
+        acc_list = li;
+      }
+      staged_chunk<MODE>(pk, sbase, lane, carry,
+                         MODE == kStore ? out + L.out_offset + 128ull * k0 + 16 * c + s : nullptr,
+                         acc);
+      __syncwarp();  // every lane is done with the stage before it is refilled
       if (MODE == kColsum) {
-#pragma unroll 1
-        for (uint32_t j = 0; j < kChunk; j++) {
-          const uint32_t p = __shfl_sync(kFull, pk, j);
-          uint32_t d[4];
-          pl_block_deltas_from((int)(p >> 16), PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
-          carry += d[0] + d[1] + d[2] + d[3];
-        }
-        __syncwarp();  // every lane is done with the stage before it is refilled
         carry += __shfl_xor_sync(kFull, carry, 1);
         carry += __shfl_xor_sync(kFull, carry, 2);
         carry += __shfl_xor_sync(kFull, carry, 4);
@@ -681,38 +747,7 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
           sc.chunk[ch] = make_uint4(carry, c1, c2, c3);
           sc.chunk_head[ch] = head ? 1u : 0u;
         }
-        continue;
       }
-      uint32_t *o = out + L.out_offset + 128ull * k0 + 16 * c + s;
-      if (MODE == kSum && acc_list != li) {
-        if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
-        acc_list = li;
-      }
-#pragma unroll 1
-      for (uint32_t j = 0; j < kChunk; j++) {
-        const uint32_t p = __shfl_sync(kFull, pk, j);
-        uint32_t d[4];
-        pl_block_deltas_from((int)(p >> 16), PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
-        uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
-        uint32_t inc = x3;
-#pragma unroll
-        for (int dd = 1; dd < 8; dd <<= 1) {
-          const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
-          if (c >= dd) inc += t;
-        }
-        const uint32_t base = carry + inc - x3;
-        carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
-        if (MODE == kSum) {
-          acc += (uint64_t)(x0 + base) + (x1 + base) + (x2 + base) + (x3 + base);
-        } else {
-          o[0] = x0 + base;
-          o[4] = x1 + base;
-          o[8] = x2 + base;
-          o[12] = x3 + base;
-          o += 128;
-        }
-      }
-      __syncwarp();  // every lane is done with the stage before it is refilled
       continue;
     }
     for (uint32_t j = 0; j < cnt; j++) {
