@@ -111,6 +111,27 @@ void orc_s4_pack128(const uint32_t in[128], unsigned b, uint32_t *out) {
 /* values are 0, so each vector is P((0,0,0,0), v).                        */
 
 static void apply_p(int kind, uint32_t t[4], uint32_t v[4]) {
+  if (kind == ORC_P_DM) {
+    /* Section 5, DM: copy the last component of the previous vector to all
+     * four components and add */
+    const uint32_t last = v[3];
+    for (int s = 0; s < 4; s++) t[s] += last;
+  } else if (kind == ORC_P_D2 || kind == ORC_P_D1) {
+    /* Section 5, D2: shift the deltas by two integers and add them to
+     * themselves, then add (v2, v3, v2, v3) */
+    uint32_t u[4] = {t[0], t[1], t[0] + t[2], t[1] + t[3]};
+    if (kind == ORC_P_D2) {
+      t[0] = u[0] + v[2];
+      t[1] = u[1] + v[3];
+      t[2] = u[2] + v[2];
+      t[3] = u[3] + v[3];
+    } else {
+      /* D1: shift that result by one integer and add it to itself, then add
+       * the last component of the previous vector to all components */
+      const uint32_t w[4] = {u[0], u[0] + u[1], u[1] + u[2], u[2] + u[3]};
+      for (int s = 0; s < 4; s++) t[s] = w[s] + v[3];
+    }
+  }
   for (int s = 0; s < 4; s++) {
     if (kind == ORC_P_D4) t[s] += v[s]; /* P(t,v) = t + v, Section 5 */
     v[s] = t[s];
@@ -164,6 +185,27 @@ void orc_d4_deltas(const uint32_t *x, size_t n, uint32_t *d) {
 
 void orc_d4_prefix(const uint32_t *d, size_t n, uint32_t *x) {
   for (size_t i = 0; i < n; i++) x[i] = d[i] + (i >= 4 ? x[i - 4] : 0u);
+}
+
+/* The value x[i] is coded against, for each kind of Section 5; positions
+ * before 0 hold `seed`.  DM: the last value of the previous 4-vector. */
+static uint32_t delta_ref(int kind, const uint32_t *x, size_t i, uint32_t seed) {
+  long long j;
+  switch (kind) {
+    case ORC_DELTA_DM: j = 4 * (long long)(i / 4) - 1; break;
+    case ORC_DELTA_D2: j = (long long)i - 2; break;
+    case ORC_DELTA_D1: j = (long long)i - 1; break;
+    default: j = (long long)i - 4; break;
+  }
+  return j >= 0 ? x[j] : seed;
+}
+
+void orc_deltas(int kind, const uint32_t *x, size_t n, uint32_t seed, uint32_t *d) {
+  for (size_t i = 0; i < n; i++) d[i] = x[i] - delta_ref(kind, x, i, seed);
+}
+
+void orc_prefix(int kind, const uint32_t *d, size_t n, uint32_t seed, uint32_t *x) {
+  for (size_t i = 0; i < n; i++) x[i] = d[i] + delta_ref(kind, x, i, seed);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -225,7 +267,13 @@ size_t orc_pl_bound(size_t n) {
 
 int orc_pl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
                   size_t *out_bytes) {
+  return orc_pl_encode_kind(x, n, ORC_DELTA_D4, out, cap, out_bytes);
+}
+
+int orc_pl_encode_kind(const uint32_t *x, size_t n, int kind, uint8_t *out,
+                       size_t cap, size_t *out_bytes) {
   if ((!x && n) || !out || !out_bytes) return ORC_EARG;
+  if (kind < ORC_DELTA_D4 || kind > ORC_DELTA_D1) return ORC_EARG;
   if (n > 0xFFFFFFFFull) return ORC_EARG;
   if (!is_sorted_distinct(x, n)) return ORC_EARG;
   if (cap < orc_pl_bound(n)) return ORC_ECAPACITY;
@@ -233,7 +281,8 @@ int orc_pl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
   const size_t nb = n / 128, np = nb * 128, meta = nb / 16;
   uint32_t *d = (uint32_t *)malloc((np ? np : 1) * sizeof(uint32_t));
   if (!d) return ORC_EARG;
-  orc_d4_deltas(x, np, d);
+  if (kind == ORC_DELTA_D4) orc_d4_deltas(x, np, d);
+  else orc_deltas(kind, x, np, 0u, d);
 
   size_t pos = 16;
   uint32_t words[128];
@@ -270,7 +319,7 @@ int orc_pl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
   wr32(out + 0, (uint32_t)n);
   wr32(out + 4, 0u);
   wr32(out + 8, (uint32_t)tail);
-  wr32(out + 12, 0u);
+  wr32(out + 12, (uint32_t)kind);
   *out_bytes = pos;
   return ORC_OK;
 }
@@ -289,14 +338,24 @@ int orc_stream_count(const uint8_t *in, size_t nbytes, size_t *n_out) {
 }
 
 static int pl_block(const uint8_t *in, size_t nbytes, size_t *pos, unsigned w,
-                    uint32_t v[4], uint32_t *out) {
+                    int pkind, uint32_t v[4], uint32_t *out) {
   uint32_t y[128];
   if (w > 32) return ORC_ECORRUPT;
   if (*pos + 16 * (size_t)w > nbytes) return ORC_ECORRUPT;
   for (unsigned q = 0; q < 4 * w; q++) y[q] = rd32(in + *pos + 4 * q);
   *pos += 16 * (size_t)w;
-  orc_s4_unpack128(y, w, ORC_P_D4, v, out);
+  orc_s4_unpack128(y, w, pkind, v, out);
   return ORC_OK;
+}
+
+/* Prefix function of Algorithm 1 for a kind of differential coding. */
+static int prefix_kind(uint32_t kind) {
+  switch (kind) {
+    case ORC_DELTA_DM: return ORC_P_DM;
+    case ORC_DELTA_D2: return ORC_P_D2;
+    case ORC_DELTA_D1: return ORC_P_D1;
+    default: return ORC_P_D4;
+  }
 }
 
 int orc_pl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
@@ -304,7 +363,9 @@ int orc_pl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
   if (!in || !n_out) return ORC_EARG;
   if (nbytes < 16) return ORC_ECORRUPT;
   const size_t n = rd32(in);
-  if (rd32(in + 4) != 0u || rd32(in + 12) != 0u) return ORC_ECORRUPT;
+  const uint32_t kind = rd32(in + 12);
+  if (rd32(in + 4) != 0u || kind > ORC_DELTA_D1) return ORC_ECORRUPT;
+  const int pkind = prefix_kind(kind);
   const size_t tail = rd32(in + 8);
   *n_out = n;
   if (n > cap) return ORC_ECAPACITY;
@@ -320,14 +381,14 @@ int orc_pl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
     for (unsigned j = 0; j < 16; j++) w[j] = in[pos + j];
     pos += 16;
     for (unsigned j = 0; j < 16; j++) {
-      rc = pl_block(in, nbytes, &pos, w[j], v, out + (16 * m + j) * 128);
+      rc = pl_block(in, nbytes, &pos, w[j], pkind, v, out + (16 * m + j) * 128);
       if (rc) return rc;
     }
   }
   for (size_t blk = meta * 16; blk < nb; blk++) {
     if (pos + 1 > nbytes) return ORC_ECORRUPT;
     unsigned w = in[pos++];
-    rc = pl_block(in, nbytes, &pos, w, v, out + blk * 128);
+    rc = pl_block(in, nbytes, &pos, w, pkind, v, out + blk * 128);
     if (rc) return rc;
   }
   if (pos + tail != nbytes) return ORC_ECORRUPT;
@@ -377,10 +438,16 @@ size_t orc_gl_bound(size_t n) {
 }
 
 /* One block: the 128 values x[0..cnt) padded so that every missing delta is
- * zero, D4 deltas against the seed (F,F,F,F), F = x[0]. */
-static void gl_block_deltas(const uint32_t *x, unsigned cnt, uint32_t d[128]) {
+ * zero, D4 deltas against the seed (F,F,F,F), F = x[0]; other kinds of
+ * Section 5 likewise against F. */
+static void gl_block_deltas(const uint32_t *x, unsigned cnt, int kind, uint32_t d[128]) {
   uint32_t xx[128];
   const uint32_t F = x[0];
+  if (kind != ORC_DELTA_D4) {
+    for (unsigned i = 0; i < 128; i++) xx[i] = i < cnt ? x[i] : delta_ref(kind, xx, i, F);
+    orc_deltas(kind, xx, 128, F, d);
+    return;
+  }
   for (unsigned i = 0; i < 128; i++) {
     if (i < cnt) xx[i] = x[i];
     else xx[i] = (i >= 4) ? xx[i - 4] : F;
@@ -404,7 +471,13 @@ static uint32_t get_bits(const uint32_t *w, size_t pos, unsigned b) {
 
 int orc_gl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
                   size_t *out_bytes) {
+  return orc_gl_encode_kind(x, n, ORC_DELTA_D4, out, cap, out_bytes);
+}
+
+int orc_gl_encode_kind(const uint32_t *x, size_t n, int kind, uint8_t *out,
+                       size_t cap, size_t *out_bytes) {
   if ((!x && n) || !out || !out_bytes) return ORC_EARG;
+  if (kind < ORC_DELTA_D4 || kind > ORC_DELTA_D1) return ORC_EARG;
   if (n > 0x7FFFFFFFull) return ORC_EARG;
   if (!is_sorted_distinct(x, n)) return ORC_EARG;
   if (cap < orc_gl_bound(n)) return ORC_ECAPACITY;
@@ -418,7 +491,7 @@ int orc_gl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
   uint32_t d[128], words[128];
   for (size_t k = 0; k < nb; k++) {
     const unsigned cnt = (unsigned)((n - 128 * k) < 128 ? (n - 128 * k) : 128);
-    gl_block_deltas(x + 128 * k, cnt, d);
+    gl_block_deltas(x + 128 * k, cnt, kind, d);
     const unsigned b = orc_max_bits(d, 128);
     if (k % 32 == 0) wr32(out + off_sbo + 4 * (k / 32), (uint32_t)wpos);
     wr32(out + off_first + 4 * k, x[128 * k]);
@@ -446,7 +519,7 @@ int orc_gl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
                       (uint32_t)off_payload,
                       (uint32_t)(total & 0xFFFFFFFFu),
                       (uint32_t)((uint64_t)total >> 32),
-                      0,
+                      (uint32_t)kind,
                       0,
                       0,
                       0};
@@ -491,6 +564,8 @@ int orc_gl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
   if (n > cap) return ORC_ECAPACITY;
   if (n && !out) return ORC_EARG;
   const uint8_t *first = in + info[4], *sbo = in + info[5], *bw = in + info[6];
+  const uint32_t kind = rd32(in + 48);
+  if (kind > ORC_DELTA_D1) return ORC_ECORRUPT;
 
   uint32_t *payload = (uint32_t *)malloc((pw + 1) * sizeof(uint32_t));
   if (!payload) return ORC_EARG;
@@ -508,12 +583,20 @@ int orc_gl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
       }
       const uint32_t F = rd32(first + 4 * k);
       uint32_t x[128];
-      for (unsigned t = 0; t < 32; t++)
-        for (unsigned s = 0; s < 4; s++) {
-          uint32_t delta = get_bits(payload + wpos, (size_t)b * (32 * s + t), b);
-          uint32_t prev = (t == 0) ? F : x[4 * (t - 1) + s];
-          x[4 * t + s] = prev + delta;
-        }
+      if (kind == ORC_DELTA_D4) {
+        for (unsigned t = 0; t < 32; t++)
+          for (unsigned s = 0; s < 4; s++) {
+            uint32_t delta = get_bits(payload + wpos, (size_t)b * (32 * s + t), b);
+            uint32_t prev = (t == 0) ? F : x[4 * (t - 1) + s];
+            x[4 * t + s] = prev + delta;
+          }
+      } else {
+        uint32_t d[128];
+        for (unsigned t = 0; t < 32; t++)
+          for (unsigned s = 0; s < 4; s++)
+            d[4 * t + s] = get_bits(payload + wpos, (size_t)b * (32 * s + t), b);
+        orc_prefix((int)kind, d, 128, F, x);
+      }
       const size_t cnt = (n - 128 * k) < 128 ? (n - 128 * k) : 128;
       for (size_t i = 0; i < cnt; i++) out[128 * k + i] = x[i];
       wpos += 4 * (size_t)b;

@@ -55,7 +55,9 @@ void orc_s4_pack128(const uint32_t in[128], unsigned b, uint32_t *out);
  * function P.  kind = ORC_P_NONE gives P(t,v) = t (plain unpack);
  * kind = ORC_P_D4 gives P(t,v) = t + v (D4, Section 5).  v is the 4-int
  * seed vector, updated in place to the last 4 outputs. */
-enum { ORC_P_NONE = 0, ORC_P_D4 = 1 };
+enum { ORC_P_NONE = 0, ORC_P_D4 = 1, ORC_P_DM = 2, ORC_P_D2 = 3, ORC_P_D1 = 4 };
+/* ORC_P_DM, ORC_P_D2, ORC_P_D1 apply the vector prefix steps Section 5 gives
+ * for DM, D2 and D1 (v: the previous output vector). */
 void orc_s4_unpack128(const uint32_t *y, unsigned b, int kind, uint32_t v[4],
                       uint32_t out[128]);
 
@@ -65,6 +67,15 @@ void orc_s4_unpack128(const uint32_t *y, unsigned b, int kind, uint32_t v[4],
 void orc_d4_deltas(const uint32_t *x, size_t n, uint32_t *d);
 /* Inverse: x[i] = d[i] + x[i-4]. */
 void orc_d4_prefix(const uint32_t *d, size_t n, uint32_t *x);
+
+/* The four kinds of differential coding of Section 5, as stored in stream
+ * headers: D4 d[i] = x[i] - x[i-4]; DM d[4t+s] = x[4t+s] - x[4t-1] (every
+ * 4-vector minus the last value of the previous one); D2 d[i] = x[i] - x[i-2];
+ * D1 d[i] = x[i] - x[i-1].  Positions before x[0] hold `seed`. */
+enum { ORC_DELTA_D4 = 0, ORC_DELTA_DM = 1, ORC_DELTA_D2 = 2, ORC_DELTA_D1 = 3 };
+void orc_deltas(int kind, const uint32_t *x, size_t n, uint32_t seed, uint32_t *d);
+/* Inverse of orc_deltas. */
+void orc_prefix(int kind, const uint32_t *d, size_t n, uint32_t seed, uint32_t *x);
 
 /* ---- varint (Section 4.1, Fig. 1b) --------------------------------------- */
 
@@ -76,15 +87,19 @@ int orc_varint_decode(const uint8_t *in, size_t nbytes, size_t n,
                       uint32_t *out, size_t *used);
 
 /* ---- S4-BP128-D4 container, paper layout "PL" (Section 4.3) ------------- *
- * header   16 bytes: u32 n, u32 layout tag (0), u32 tail_bytes, u32 0
+ * header   16 bytes: u32 n, u32 layout tag (0), u32 tail_bytes, u32 kind of
+ *          differential coding (ORC_DELTA_*, 0 = D4)
  * then     floor(nb/16) meta-blocks: 16 width bytes, then 16 packed blocks
  * then     nb mod 16 leftover blocks: 1 width byte, then the packed block
  * then     the n mod 128 remaining integers as varint of D1 gaps from the
  *          previous integer (0 before the first)
- * where nb = floor(n/128) and blocks hold D4 deltas carried across blocks. */
+ * where nb = floor(n/128) and blocks hold D4 (or DM, D2, D1) deltas carried
+ * across blocks. */
 size_t orc_pl_bound(size_t n);
 int orc_pl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
                   size_t *out_bytes);
+int orc_pl_encode_kind(const uint32_t *x, size_t n, int kind, uint8_t *out,
+                       size_t cap, size_t *out_bytes);
 /* Reads n from the header; fails with ORC_ECAPACITY if n > cap. */
 int orc_pl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
                   size_t *n_out);
@@ -98,10 +113,15 @@ int orc_stream_count(const uint8_t *in, size_t nbytes, size_t *n_out);
  *   bw[k] = bit width; the block's 4*bw[k] words hold the 128 deltas in
  *   column-major order: delta of in-block position 4t+s (row t, column s)
  *   at bit bw*(32s+t) of the block's LSB-first bit string;
- *   sbo[q] = word offset of block 32q in the payload (q <= nsuper). */
+ *   sbo[q] = word offset of block 32q in the payload (q <= nsuper).
+ * Header word 12 holds the kind of differential coding (ORC_DELTA_*); for
+ * DM, D2 and D1 the block's deltas are taken the same way against the seed
+ * F, and padding again makes the missing deltas zero. */
 size_t orc_gl_bound(size_t n);
 int orc_gl_encode(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
                   size_t *out_bytes);
+int orc_gl_encode_kind(const uint32_t *x, size_t n, int kind, uint8_t *out,
+                       size_t cap, size_t *out_bytes);
 int orc_gl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
                   size_t *n_out);
 /* Header fields of a GL stream: nblocks, offsets of first[], sbo[], bw[],

@@ -62,6 +62,8 @@ class Oracle:
         L.orc_s4_unpack128.argtypes = [_u32p, C.c_uint, C.c_int, _u32p, _u32p]
         L.orc_d4_deltas.argtypes = [_u32p, _sz, _u32p]
         L.orc_d4_prefix.argtypes = [_u32p, _sz, _u32p]
+        L.orc_deltas.argtypes = [C.c_int, _u32p, _sz, C.c_uint32, _u32p]
+        L.orc_prefix.argtypes = [C.c_int, _u32p, _sz, C.c_uint32, _u32p]
         L.orc_varint_encode.argtypes = [_u32p, _sz, _u8p]
         L.orc_varint_encode.restype = _sz
         L.orc_varint_decode.argtypes = [_u8p, _sz, _sz, _u32p, C.POINTER(_sz)]
@@ -71,6 +73,9 @@ class Oracle:
             getattr(L, f).restype = _sz
         for f in ("orc_pl_encode", "orc_gl_encode"):
             getattr(L, f).argtypes = [_u32p, _sz, _u8p, _sz, C.POINTER(_sz)]
+            getattr(L, f).restype = C.c_int
+        for f in ("orc_pl_encode_kind", "orc_gl_encode_kind"):
+            getattr(L, f).argtypes = [_u32p, _sz, C.c_int, _u8p, _sz, C.POINTER(_sz)]
             getattr(L, f).restype = C.c_int
         for f in ("orc_pl_decode", "orc_gl_decode"):
             getattr(L, f).argtypes = [_u8p, _sz, _u32p, _sz, C.POINTER(_sz)]
@@ -117,12 +122,18 @@ class Oracle:
         self.lib.orc_s4_pack128(v, b, out)
         return out[: 4 * b]
 
-    def s4_unpack128(self, words, b: int, d4: bool = True, seed=(0, 0, 0, 0)):
+    # prefix functions of Algorithm 1 (ORC_P_*)
+    P_NONE, P_D4, P_DM, P_D2, P_D1 = 0, 1, 2, 3, 4
+
+    def s4_unpack128(self, words, b: int, d4: bool = True, seed=(0, 0, 0, 0),
+                     kind: int | None = None):
+        """Algorithm 1; kind (P_*) overrides d4 (True: P_D4, False: P_NONE)."""
         w = np.zeros(max(1, 4 * b + 4), np.uint32)
         w[: 4 * b] = _u32(words)[: 4 * b]
         v = _u32(seed).copy()
         out = np.zeros(128, np.uint32)
-        self.lib.orc_s4_unpack128(w, b, 1 if d4 else 0, v, out)
+        k = kind if kind is not None else (1 if d4 else 0)
+        self.lib.orc_s4_unpack128(w, b, k, v, out)
         return out, v
 
     # -- differential coding ---------------------------------------------------
@@ -136,6 +147,21 @@ class Oracle:
         d = _u32(d)
         x = np.zeros(max(1, d.size), np.uint32)
         self.lib.orc_d4_prefix(d, d.size, x)
+        return x[: d.size]
+
+    # kinds of differential coding (Section 5), as stored in stream headers
+    D4, DM, D2, D1 = 0, 1, 2, 3
+
+    def deltas(self, kind: int, x, seed: int = 0) -> np.ndarray:
+        x = _u32(x)
+        d = np.zeros(max(1, x.size), np.uint32)
+        self.lib.orc_deltas(kind, x, x.size, seed, d)
+        return d[: x.size]
+
+    def prefix(self, kind: int, d, seed: int = 0) -> np.ndarray:
+        d = _u32(d)
+        x = np.zeros(max(1, d.size), np.uint32)
+        self.lib.orc_prefix(kind, d, d.size, seed, x)
         return x[: d.size]
 
     # -- varint ---------------------------------------------------------------
@@ -179,13 +205,27 @@ class Oracle:
             raise OracleError(rc, fn.__name__)
         return out[: got.value]
 
-    def pl_encode(self, x) -> bytes:
+    def _encode_kind(self, fn, bound, x, kind: int) -> bytes:
+        x = _u32(x)
+        cap = int(bound(x.size))
+        out = np.zeros(cap, np.uint8)
+        nbytes = _sz(0)
+        rc = fn(x, x.size, kind, out, cap, C.byref(nbytes))
+        if rc:
+            raise OracleError(rc, fn.__name__)
+        return out[: nbytes.value].tobytes()
+
+    def pl_encode(self, x, kind: int = 0) -> bytes:
+        if kind:
+            return self._encode_kind(self.lib.orc_pl_encode_kind, self.lib.orc_pl_bound, x, kind)
         return self._encode(self.lib.orc_pl_encode, self.lib.orc_pl_bound, x)
 
     def pl_decode(self, data: bytes) -> np.ndarray:
         return self._decode(self.lib.orc_pl_decode, data)
 
-    def gl_encode(self, x) -> bytes:
+    def gl_encode(self, x, kind: int = 0) -> bytes:
+        if kind:
+            return self._encode_kind(self.lib.orc_gl_encode_kind, self.lib.orc_gl_bound, x, kind)
         return self._encode(self.lib.orc_gl_encode, self.lib.orc_gl_bound, x)
 
     def gl_decode(self, data: bytes) -> np.ndarray:

@@ -56,16 +56,33 @@ def varint(values) -> bytes:
     return bytes(out)
 
 
-def pl_stream(x) -> bytes:
-    """The S4-BP128-D4 paper layout of Section 4.3 with our header/tail
-    reading, built from the prose: D4 deltas against (0,0,0,0), meta-blocks
-    of 16 widths + 16 blocks, leftover blocks with a width byte each, varint
-    of D1 gaps for the last n mod 128 integers."""
+# kinds of differential coding (Section 5) as stored in stream headers
+D4, DM, D2, D1 = 0, 1, 2, 3
+
+
+def reference(kind: int, x, i: int, seed: int) -> int:
+    """The earlier value that x[i] is coded against (Section 5): D4 x[i-4],
+    DM the last value of the previous 4-vector, D2 x[i-2], D1 x[i-1];
+    positions before the list hold `seed`."""
+    j = {D4: i - 4, DM: 4 * (i // 4) - 1, D2: i - 2, D1: i - 1}[kind]
+    return x[j] if j >= 0 else seed
+
+
+def deltas(kind: int, x, seed: int = 0):
+    return [(x[i] - reference(kind, x, i, seed)) % 2**32 for i in range(len(x))]
+
+
+def pl_stream(x, kind: int = D4) -> bytes:
+    """The S4-BP128 paper layout of Section 4.3 with our header/tail
+    reading, built from the prose: deltas of the given kind against a zero
+    seed, meta-blocks of 16 widths + 16 blocks, leftover blocks with a width
+    byte each, varint of D1 gaps for the last n mod 128 integers; header
+    {n, 0, tail bytes, kind}."""
     x = [int(v) for v in x]
     n = len(x)
     nb = n // 128
     np_ = 128 * nb
-    d = [(x[i] - (x[i - 4] if i >= 4 else 0)) % 2**32 for i in range(np_)]
+    d = deltas(kind, x[:np_])
     widths = [bits_of(max(d[128 * k:128 * k + 128])) for k in range(nb)]
     body = bytearray()
     for m in range(nb // 16):
@@ -82,11 +99,11 @@ def pl_stream(x) -> bytes:
         gaps.append((v - prev) % 2**32)
         prev = v
     tail = varint(gaps)
-    hdr = le32([n, 0, len(tail), 0])
+    hdr = le32([n, 0, len(tail), kind])
     return hdr + bytes(body) + tail
 
 
-def gl_stream(x) -> bytes:
+def gl_stream(x, kind: int = D4) -> bytes:
     """GL layout (ours): see the oracle header for the field list."""
     x = [int(v) for v in x]
     n = len(x)
@@ -105,10 +122,9 @@ def gl_stream(x) -> bytes:
         blk = x[128 * k:128 * k + 128]
         F = blk[0]
         full = list(blk)
-        for i in range(len(blk), 128):
-            full.append(full[i - 4] if i >= 4 else F)
-        d = [(full[i] - (full[i - 4] if i >= 4 else F)) % 2**32
-             for i in range(128)]
+        for i in range(len(blk), 128):  # padding: every missing delta is zero
+            full.append(reference(kind, full, i, F))
+        d = deltas(kind, full, F)
         b = bits_of(max(d))
         if k % 32 == 0:
             sbo.append(len(payload))
@@ -119,7 +135,7 @@ def gl_stream(x) -> bytes:
     total = off_payload + 4 * len(payload)
     out = bytearray(total)
     hdr = [0x344C4742, 1, n, nb, ns, len(payload), off_first, off_sbo, off_bw,
-           off_payload, total & 0xFFFFFFFF, total >> 32, 0, 0, 0, 0]
+           off_payload, total & 0xFFFFFFFF, total >> 32, kind, 0, 0, 0]
     out[0:64] = le32(hdr)
     out[off_first:off_first + 4 * nb] = le32(first)
     out[off_sbo:off_sbo + 4 * (ns + 1)] = le32(sbo)

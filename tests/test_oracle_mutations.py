@@ -44,6 +44,15 @@ MUTANTS = [
     ("v3 wrong quarter", "F = (f[j + T - 1] >= ri) ? f + j : f + j + T;",
      "F = (f[j + T - 1] >= ri) ? f + j : f + j + 2 * T;"),
     ("simd gallop skips bsearch", "j += lo * T;", "j += delta;"),
+    ("dm against x[4t-2]", "case ORC_DELTA_DM: j = 4 * (long long)(i / 4) - 1; break;",
+     "case ORC_DELTA_DM: j = 4 * (long long)(i / 4) - 2; break;"),
+    ("d2 prefix takes v3 for lane 0", "t[0] = u[0] + v[2];", "t[0] = u[0] + v[3];"),
+    ("d1 second shift by two", "const uint32_t w[4] = {u[0], u[0] + u[1], u[1] + u[2], u[2] + u[3]};",
+     "const uint32_t w[4] = {u[0], u[1], u[0] + u[2], u[1] + u[3]};"),
+    ("dm prefix adds lane-wise", "for (int s = 0; s < 4; s++) t[s] += last;",
+     "for (int s = 0; s < 4; s++) t[s] += v[s];"),
+    ("gl kind not in header", "                      (uint32_t)kind,\n", "                      0u,\n"),
+    ("pl decode ignores kind", "const int pkind = prefix_kind(kind);", "const int pkind = ORC_P_D4;"),
 ]
 
 

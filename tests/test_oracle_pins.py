@@ -126,6 +126,83 @@ def test_pl_arithmetic_progression_widths_and_size(orc):
     assert data[16:32] == bytes([b] * 16)
 
 
+# ---- DM, D2, D1 (Section 5) ---------------------------------------------------
+
+KINDS = [0, 1, 2, 3]  # D4, DM, D2, D1 as stored in stream headers
+
+
+@pytest.mark.parametrize("c", [1, 3, 77777])
+def test_variant_arithmetic_progression_closed_forms(orc, c):
+    """x_i = c*i (i = 1..n): D1 deltas are all c; D2 (c, 2c, 2c, ...); DM
+    (c, 2c, 3c, 4c) repeated (every 4-vector minus the last value of the
+    previous one); D4 (c, 2c, 3c, 4c, 4c, ...)."""
+    n = 1000
+    x = (c * np.arange(1, n + 1, dtype=np.uint64)).astype(np.uint32)
+    want = {
+        orc.D1: [c] * n,
+        orc.D2: [c] + [2 * c] * (n - 1),
+        orc.DM: [c, 2 * c, 3 * c, 4 * c] * (n // 4),
+        orc.D4: [c, 2 * c, 3 * c] + [4 * c] * (n - 3),
+    }
+    for kind, w in want.items():
+        d = orc.deltas(kind, x)
+        assert d.tolist() == [v & M32 for v in w], kind
+        assert np.array_equal(orc.prefix(kind, d), x), kind
+
+
+def test_variant_mean_delta_ratios(orc):
+    """Section 5 expects deltas 4x (D4), 2.5x (DM) and 2x (D2) larger than
+    D1's on average: exactly so in expectation for independent gaps."""
+    rng = np.random.default_rng(11)
+    gaps = rng.integers(1, 64, 400_000, dtype=np.uint64)
+    x = np.cumsum(gaps).astype(np.uint32)
+    m1 = orc.deltas(orc.D1, x)[4:].astype(np.float64).mean()
+    for kind, ratio in ((orc.D4, 4.0), (orc.DM, 2.5), (orc.D2, 2.0)):
+        m = orc.deltas(kind, x)[4:].astype(np.float64).mean()
+        assert abs(m / m1 - ratio) < 0.02 * ratio, (kind, m / m1)
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_variant_integrated_unpack(orc, kind):
+    """Algorithm 1 with the vector prefix steps of Section 5 (DM: add the
+    last value of the previous vector; D2: shift by two and add, then add
+    (v2, v3, v2, v3); D1: the D2 steps, a shift by one and add, then the last
+    value) equals the prefix of the definition, from any seed vector."""
+    rng = np.random.default_rng(100 + kind)
+    for b in (0, 1, 7, 18, 31, 32):
+        for _ in range(4):
+            d = [int(v) for v in rng.integers(0, 1 << b, 128, dtype=np.uint64)] if b else [0] * 128
+            prev = [int(v) for v in rng.integers(0, 1 << 32, 4, dtype=np.uint64)]
+            words = brute.s4_block_words(d, b)
+            got, last = orc.s4_unpack128(words, b, kind=kind + 1, seed=prev)
+            x = list(prev)
+            for p in range(128):  # the definition, on prev followed by the block
+                x.append((d[p] + brute.reference(kind, x, 4 + p, 0)) % 2**32)
+            assert got.tolist() == x[4:], (kind, b)
+            assert last.tolist() == x[-4:], (kind, b)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [0, 1, 129, 2047, 2048 + 128 + 5, 2 * 2048 + 15 * 128 + 127])
+def test_variant_streams_match_bitwise_construction(orc, kind, n):
+    rng = np.random.default_rng(50 * kind + n)
+    x = _sorted_distinct(rng, n, 1 << 28)
+    pl = orc.pl_encode(x, kind)
+    gl = orc.gl_encode(x, kind)
+    assert pl == brute.pl_stream(x, kind)
+    assert gl == brute.gl_stream(x, kind)
+    assert np.array_equal(orc.pl_decode(pl), x)
+    assert np.array_equal(orc.gl_decode(gl), x)
+
+
+def test_variant_sizes_order(orc):
+    """Smaller deltas, fewer bits: on the same list D1 <= D2 <= DM <= D4."""
+    rng = np.random.default_rng(3)
+    x = np.sort(rng.choice(1 << 26, 200_000, replace=False)).astype(np.uint32)
+    sizes = [len(orc.pl_encode(x, k)) for k in (orc.D1, orc.D2, orc.DM, orc.D4)]
+    assert sizes == sorted(sizes)
+
+
 # ---- containers -------------------------------------------------------------
 
 EDGE_N = [0, 1, 2, 3, 4, 5, 127, 128, 129, 255, 256, 257, 2047, 2048, 2049,
