@@ -70,6 +70,26 @@ typedef enum {
   BP_LAYOUT_GPU = 1
 } bp_layout;
 
+/* Kind of differential coding of a stream (Section 5), stored in its
+ * header (word 3 of the paper layout's, word 12 of the GPU layout's):
+ *   D4  delta[i] = x[i] - x[i-4]                       (the default)
+ *   DM  delta[4t+s] = x[4t+s] - x[4t-1]   (every 4-vector minus the last
+ *                                          value of the previous one)
+ *   D2  delta[i] = x[i] - x[i-2]
+ *   D1  delta[i] = x[i] - x[i-1]
+ * In the paper layout the values before the list are 0 and deltas run on
+ * from block to block; in the GPU layout every block starts again from its
+ * first value.  Decoding reads the kind from the header.  The fused
+ * intersection paths (bp_intersect_pair with BP_MODE_FUSED or AUTO,
+ * bp_intersect_pair_noalloc, bp_query_batch) take D4 streams only and record
+ * BP_ERR_ARG for others; BP_MODE_UNFUSED and bp_query_one take every kind. */
+typedef enum {
+  BP_DELTA_D4 = 0,
+  BP_DELTA_DM = 1,
+  BP_DELTA_D2 = 2,
+  BP_DELTA_D1 = 3
+} bp_delta;
+
 /* One list of a batch.  Filled by the caller except unit_base, which
  * bp_plan_lists() fills. */
 typedef struct bp_list {
@@ -122,10 +142,19 @@ size_t bp_encode_bound(size_t n, int layout);
 int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
               size_t cap, size_t *out_bytes, int nthreads);
 
+/* bp_encode with the kind of differential coding `delta` (bp_delta);
+ * bp_encode is this call with BP_DELTA_D4.  BP_ERR_ARG for an unknown kind. */
+int bp_encode_kind(const uint32_t *in, size_t n, int layout, int delta,
+                   uint8_t *out, size_t cap, size_t *out_bytes, int nthreads);
+
 /* Parse a stream header on the host: *n_out = number of integers,
  * *layout_out = its layout.  BP_ERR_CORRUPT if the header is invalid. */
 int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
                    int *layout_out);
+
+/* The kind of differential coding (bp_delta) of a stream whose header
+ * bp_stream_info accepts.  BP_ERR_CORRUPT otherwise. */
+int bp_stream_kind(const uint8_t *enc, size_t enc_bytes, int *delta_out);
 
 /* Index builder: encode `count` lists (list i = values[offs[i] ..
  * offs[i+1]), strictly increasing) in BP_LAYOUT_GPU back to back into out

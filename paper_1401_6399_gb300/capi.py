@@ -59,7 +59,9 @@ def _decl(name, restype, *argtypes):
 _decl("bp_status_string", C.c_char_p, _int)
 _decl("bp_encode_bound", _sz, _sz, _int)
 _decl("bp_encode", _int, _vp, _sz, _int, _vp, _sz, C.POINTER(_sz), _int)
+_decl("bp_encode_kind", _int, _vp, _sz, _int, _int, _vp, _sz, C.POINTER(_sz), _int)
 _decl("bp_stream_info", _int, _vp, _sz, C.POINTER(_u32), C.POINTER(_int))
+_decl("bp_stream_kind", _int, _vp, _sz, C.POINTER(_int))
 _decl("bp_plan_lists", _u64, _vp, _u32)
 _decl("bp_index_bound", _sz, _vp, _u32)
 _decl("bp_index_encode", _int, _vp, _vp, _u32, _vp, _sz, _vp, C.POINTER(_sz), _int)
@@ -114,15 +116,31 @@ def bp_encode_bound(n: int, layout: int) -> int:
     return int(lib.bp_encode_bound(n, layout))
 
 
-def bp_encode(x, layout: int, nthreads: int = 1) -> np.ndarray:
+# kinds of differential coding (bp_delta)
+BP_DELTA_D4, BP_DELTA_DM, BP_DELTA_D2, BP_DELTA_D1 = 0, 1, 2, 3
+
+
+def bp_encode(x, layout: int, nthreads: int = 1, delta: int = BP_DELTA_D4) -> np.ndarray:
     """Encode a sorted distinct uint32 array; returns the stream as uint8."""
     x = np.ascontiguousarray(x, np.uint32)
     cap = bp_encode_bound(x.size, layout)
     out = np.empty(max(cap, 16), np.uint8)
     nbytes = _sz(0)
-    check(lib.bp_encode(x.ctypes.data if x.size else None, x.size, layout, out.ctypes.data,
-                        cap, C.byref(nbytes), nthreads), "bp_encode")
+    if delta == BP_DELTA_D4:
+        rc = lib.bp_encode(x.ctypes.data if x.size else None, x.size, layout, out.ctypes.data,
+                           cap, C.byref(nbytes), nthreads)
+    else:
+        rc = lib.bp_encode_kind(x.ctypes.data if x.size else None, x.size, layout, delta,
+                                out.ctypes.data, cap, C.byref(nbytes), nthreads)
+    check(rc, "bp_encode")
     return out[: nbytes.value]
+
+
+def bp_stream_kind(enc) -> int:
+    enc = np.ascontiguousarray(enc, np.uint8)
+    k = _int(0)
+    check(lib.bp_stream_kind(enc.ctypes.data, enc.size, C.byref(k)), "bp_stream_kind")
+    return int(k.value)
 
 
 def bp_stream_info(enc) -> tuple[int, int]:

@@ -17,6 +17,18 @@ inline unsigned width_of(uint32_t v) { return v ? 32u - (unsigned)__builtin_clz(
 
 inline void put_le32(uint8_t *p, uint32_t v) { std::memcpy(p, &v, 4); }
 
+// Section 5: the index of the earlier value that x[g] is coded against --
+// D4 g-4, DM the last value of the previous 4-vector, D2 g-2, D1 g-1 --
+// negative when the value lies before the list (or block).
+inline int64_t ref_index(int kind, int64_t g) {
+  switch (kind) {
+    case BP_DELTA_DM: return 4 * (g / 4) - 1;
+    case BP_DELTA_D2: return g - 2;
+    case BP_DELTA_D1: return g - 1;
+    default: return g - 4;
+  }
+}
+
 // Run f(lo, hi) over [0, count) split into `nthreads` contiguous ranges.
 template <class F>
 void parallel_ranges(size_t count, int nthreads, F f) {
@@ -53,17 +65,20 @@ void pack_s4(const uint32_t *d, unsigned b, uint32_t *w) {
   }
 }
 
-int encode_paper(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
+// Delta of list position g (the values before the list are 0).
+inline uint32_t pl_delta(int kind, const uint32_t *x, size_t g) {
+  const int64_t j = ref_index(kind, (int64_t)g);
+  return x[g] - (j >= 0 ? x[j] : 0u);
+}
+
+int encode_paper(const uint32_t *x, size_t n, int kind, uint8_t *out, size_t cap,
                  size_t *out_bytes, int nthreads) {
   const size_t nb = n / 128, np = nb * 128, meta = nb / 16;
   std::vector<uint8_t> widths(nb);
   parallel_ranges(nb, nthreads, [&](size_t lo, size_t hi) {
     for (size_t k = lo; k < hi; k++) {
       uint32_t m = 0;
-      for (unsigned i = 0; i < 128; i++) {
-        const size_t g = 128 * k + i;
-        m |= x[g] - (g >= 4 ? x[g - 4] : 0u);
-      }
+      for (unsigned i = 0; i < 128; i++) m |= pl_delta(kind, x, 128 * k + i);
       widths[k] = (uint8_t)width_of(m);  // OR has the same width as the max
     }
   });
@@ -98,16 +113,13 @@ int encode_paper(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
   put_le32(out + 0, (uint32_t)n);
   put_le32(out + 4, 0u);
   put_le32(out + 8, (uint32_t)tail);
-  put_le32(out + 12, 0u);
+  put_le32(out + 12, (uint32_t)kind);
   for (size_t m = 0; m < meta; m++) std::memcpy(out + boff[16 * m] - 16, &widths[16 * m], 16);
   for (size_t k = 16 * meta; k < nb; k++) out[boff[k] - 1] = widths[k];
   parallel_ranges(nb, nthreads, [&](size_t lo, size_t hi) {
     uint32_t d[128], w[128];
     for (size_t k = lo; k < hi; k++) {
-      for (unsigned i = 0; i < 128; i++) {
-        const size_t g = 128 * k + i;
-        d[i] = x[g] - (g >= 4 ? x[g - 4] : 0u);
-      }
+      for (unsigned i = 0; i < 128; i++) d[i] = pl_delta(kind, x, 128 * k + i);
       pack_s4(d, widths[k], w);
       std::memcpy(out + boff[k], w, 16 * (size_t)widths[k]);
     }
@@ -133,26 +145,29 @@ void pack_gl(const uint32_t *d, unsigned b, uint32_t *w) {
     }
 }
 
-// Deltas of block k with the seed (F,F,F,F); a short last block is padded
-// so that every missing delta is zero.
-void gl_deltas(const uint32_t *x, size_t n, size_t k, uint32_t *d) {
+// Deltas of block k, the values before the block being F = x[128k]; a
+// short last block is padded so that every missing delta is zero.
+void gl_deltas(const uint32_t *x, size_t n, size_t k, int kind, uint32_t *d) {
   const size_t base = 128 * k;
   const unsigned cnt = (unsigned)std::min<size_t>(128, n - base);
   const uint32_t F = x[base];
   uint32_t xx[128];
-  for (unsigned i = 0; i < 128; i++)
-    xx[i] = i < cnt ? x[base + i] : (i >= 4 ? xx[i - 4] : F);
-  for (unsigned i = 0; i < 128; i++) d[i] = xx[i] - (i >= 4 ? xx[i - 4] : F);
+  for (unsigned i = 0; i < 128; i++) {
+    const int64_t j = ref_index(kind, i);
+    const uint32_t ref = j >= 0 ? xx[j] : F;
+    xx[i] = i < cnt ? x[base + i] : ref;
+    d[i] = xx[i] - ref;
+  }
 }
 
-int encode_gpu(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
+int encode_gpu(const uint32_t *x, size_t n, int kind, uint8_t *out, size_t cap,
                size_t *out_bytes, int nthreads) {
   const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(n);
   std::vector<uint8_t> widths(g.nblocks);
   parallel_ranges(g.nblocks, nthreads, [&](size_t lo, size_t hi) {
     uint32_t d[128];
     for (size_t k = lo; k < hi; k++) {
-      gl_deltas(x, n, k, d);
+      gl_deltas(x, n, k, kind, d);
       uint32_t m = 0;
       for (unsigned i = 0; i < 128; i++) m |= d[i];
       widths[k] = (uint8_t)width_of(m);
@@ -174,7 +189,7 @@ int encode_gpu(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
                       (uint32_t)g.nsuper, (uint32_t)w, (uint32_t)g.off_first,
                       (uint32_t)g.off_sbo, (uint32_t)g.off_bw,
                       (uint32_t)g.off_payload, (uint32_t)(total & 0xFFFFFFFFu),
-                      (uint32_t)((uint64_t)total >> 32), 0, 0, 0, 0};
+                      (uint32_t)((uint64_t)total >> 32), (uint32_t)kind, 0, 0, 0};
   std::memcpy(out, hdr, 64);
   for (size_t q = 0; q <= g.nsuper; q++)
     put_le32(out + g.off_sbo + 4 * q, (uint32_t)woff[std::min(32 * q, g.nblocks)]);
@@ -183,7 +198,7 @@ int encode_gpu(const uint32_t *x, size_t n, uint8_t *out, size_t cap,
     uint32_t d[128], wb[128];
     for (size_t k = lo; k < hi; k++) {
       put_le32(out + g.off_first + 4 * k, x[128 * k]);
-      gl_deltas(x, n, k, d);
+      gl_deltas(x, n, k, kind, d);
       pack_gl(d, widths[k], wb);
       std::memcpy(out + g.off_payload + 4 * woff[k], wb, 16 * (size_t)widths[k]);
     }
@@ -198,7 +213,7 @@ size_t gl_size(const uint32_t *x, size_t n) {
   uint64_t w = 0;
   uint32_t d[128];
   for (size_t k = 0; k < g.nblocks; k++) {
-    gl_deltas(x, n, k, d);
+    gl_deltas(x, n, k, BP_DELTA_D4, d);
     uint32_t m = 0;
     for (unsigned i = 0; i < 128; i++) m |= d[i];
     w += 4 * width_of(m);
@@ -246,7 +261,7 @@ int bp_index_encode(const uint32_t *values, const uint64_t *offs, uint32_t count
     for (size_t i = lo; i < hi; i++) {
       size_t got = 0;
       const size_t n = offs[i + 1] - offs[i];
-      rc[i] = encode_gpu(values + offs[i], n, out + lists[i].enc_offset,
+      rc[i] = encode_gpu(values + offs[i], n, BP_DELTA_D4, out + lists[i].enc_offset,
                          bp_encode_bound(n, BP_LAYOUT_GPU), &got, 1);
       if (rc[i] == BP_OK && got != sizes[i]) rc[i] = BP_ERR_ARG;
       const size_t pad = bp_fmt::up16(sizes[i]) - sizes[i];
@@ -270,14 +285,20 @@ size_t bp_encode_bound(size_t n, int layout) {
 
 int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
               size_t cap, size_t *out_bytes, int nthreads) {
+  return bp_encode_kind(in, n, layout, BP_DELTA_D4, out, cap, out_bytes, nthreads);
+}
+
+int bp_encode_kind(const uint32_t *in, size_t n, int layout, int delta, uint8_t *out,
+                   size_t cap, size_t *out_bytes, int nthreads) {
   if (!out || !out_bytes || (n && !in)) return BP_ERR_ARG;
   if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (delta < BP_DELTA_D4 || delta > BP_DELTA_D1) return BP_ERR_ARG;
   if (n > bp_fmt::kMaxList) return BP_ERR_ARG;
   for (size_t i = 1; i < n; i++)
     if (in[i] <= in[i - 1]) return BP_ERR_UNSORTED;
   if (cap < bp_encode_bound(n, layout)) return BP_ERR_CAPACITY;
-  return layout == BP_LAYOUT_PAPER ? encode_paper(in, n, out, cap, out_bytes, nthreads)
-                                   : encode_gpu(in, n, out, cap, out_bytes, nthreads);
+  return layout == BP_LAYOUT_PAPER ? encode_paper(in, n, delta, out, cap, out_bytes, nthreads)
+                                   : encode_gpu(in, n, delta, out, cap, out_bytes, nthreads);
 }
 
 int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
@@ -286,7 +307,7 @@ int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
   uint32_t h[16];
   if (enc_bytes < 16) return BP_ERR_CORRUPT;
   std::memcpy(h, enc, 16);
-  if (h[1] == 0u && h[3] == 0u) {
+  if (h[1] == 0u && h[3] <= (uint32_t)BP_DELTA_D1) {
     *n_out = h[0];
     *layout_out = BP_LAYOUT_PAPER;
     return BP_OK;
@@ -299,11 +320,24 @@ int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
     if (h[3] != g.nblocks || h[4] != g.nsuper || h[9] != g.off_payload ||
         total != g.off_payload + 4ull * h[5] || total > enc_bytes)
       return BP_ERR_CORRUPT;
+    if (h[12] > (uint32_t)BP_DELTA_D1) return BP_ERR_CORRUPT;
     *n_out = h[2];
     *layout_out = BP_LAYOUT_GPU;
     return BP_OK;
   }
   return BP_ERR_CORRUPT;
+}
+
+int bp_stream_kind(const uint8_t *enc, size_t enc_bytes, int *delta_out) {
+  uint32_t n = 0;
+  int layout = 0;
+  if (!delta_out) return BP_ERR_ARG;
+  const int rc = bp_stream_info(enc, enc_bytes, &n, &layout);
+  if (rc != BP_OK) return rc;
+  uint32_t w;
+  std::memcpy(&w, enc + (layout == BP_LAYOUT_PAPER ? 12 : 48), 4);
+  *delta_out = (int)w;
+  return BP_OK;
 }
 
 uint64_t bp_plan_lists(bp_list *lists, uint32_t count) {

@@ -57,6 +57,22 @@ def test_encoder_matches_oracle_bytes(orc, layout):
         assert capi.bp_stream_info(np.frombuffer(want, np.uint8)) == (x.size, layout)
 
 
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_encoder_kinds_match_oracle_bytes(orc, layout, kind):
+    """DM, D2 and D1 streams (Section 5) byte for byte as the oracle writes
+    them, with the kind readable from the header."""
+    rng = np.random.default_rng(43 + kind)
+    for x in _lists(rng)[::2]:
+        want = orc.pl_encode(x, kind) if layout == 0 else orc.gl_encode(x, kind)
+        for nt in (1, 4):
+            got = capi.bp_encode(x, layout, nthreads=nt, delta=kind).tobytes()
+            assert got == want, (layout, kind, x.size, nt)
+        enc = np.frombuffer(want, np.uint8)
+        assert capi.bp_stream_info(enc) == (x.size, layout)
+        assert capi.bp_stream_kind(enc) == kind
+
+
 def test_encoder_rejects_unsorted_and_small_buffers():
     with pytest.raises(capi.BPError) as e:
         capi.bp_encode(np.array([5, 4], np.uint32), 0)
