@@ -162,6 +162,14 @@ def encode_all(lists, layout: int):
         return list(ex.map(lambda x: capi.bp_encode(x, layout, nthreads=nt), lists))
 
 
+def encode_all_kind(lists, layout: int, kind: int):
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1401_6399_gb300 import capi
+    nt = max(1, min(8, (os.cpu_count() or 8) // 2))
+    with ThreadPoolExecutor(max_workers=min(len(lists), 8)) as ex:
+        return list(ex.map(lambda x: capi.bp_encode(x, layout, nthreads=nt, delta=kind), lists))
+
+
 def kernel_sha() -> str:
     h = hashlib.sha256()
     for f in ("common.cuh", "bulk.cuh", "gl_block.cuh", "decode_gl.cu", "format.h", "decode.h"):
@@ -672,6 +680,26 @@ def run_ours(args, rank, world, local):
             "gints": round(total_n / (ms_p * 1e-3) / 1e9, 2), "ms": round(ms_p, 4),
             "bits_per_int": round(8 * pbatch.compressed_bytes / total_n, 3)}
         del pbatch
+        # the other kinds of differential coding (Section 5), both layouts
+        kinds = {}
+        for kname, kind in (("DM", capi.BP_DELTA_DM), ("D2", capi.BP_DELTA_D2),
+                            ("D1", capi.BP_DELTA_D1)):
+            for lname, lay in (("gl", capi.BP_LAYOUT_GPU), ("pl", capi.BP_LAYOUT_PAPER)):
+                encs_k = encode_all_kind(lists, lay, kind)
+                kb = api.ListBatch(encs_k, [n] * L, lay)
+                with torch.cuda.stream(stream):
+                    kb.decode_into(out, status, stream)
+                stream.synchronize()
+                assert int(status.item()) == 0
+                assert torch.equal(out, torch.from_numpy(np.concatenate(lists).view(np.int32))
+                                   .to("cuda"))
+                ms_k = time_launches(stream, lambda: kb.decode_into(out, status, stream),
+                                     max(3, reps // 5), 1)
+                kinds[f"{lname}_{kname}"] = {
+                    "gints": round(total_n / (ms_k * 1e-3) / 1e9, 2), "ms": round(ms_k, 4),
+                    "bits_per_int": round(8 * kb.compressed_bytes / total_n, 3)}
+                del kb, encs_k
+        extra["decode_kinds_uniform"] = kinds
         del out
         torch.cuda.empty_cache()
         try:

@@ -30,6 +30,7 @@ __device__ __forceinline__ uint32_t low_mask(int b) {
 // A GL stream as seen from the device after its header has been checked.
 struct GlView {
   uint32_t n, nblocks, nsuper, pw;
+  uint32_t kind;  // differential coding (0 D4, 1 DM, 2 D2, 3 D1)
   const uint32_t *first;
   const uint32_t *sbo;
   const uint8_t *bw;
@@ -41,15 +42,16 @@ struct GlView {
 __device__ __forceinline__ bool gl_view(const uint8_t *enc, uint64_t enc_bytes, GlView &v) {
   if (enc_bytes < bp_fmt::kGlHeader || (reinterpret_cast<uintptr_t>(enc) & 15u) != 0) return false;
   const uint4 *h4 = reinterpret_cast<const uint4 *>(enc);
-  const uint4 a = __ldg(h4 + 0), b = __ldg(h4 + 1), c = __ldg(h4 + 2);
+  const uint4 a = __ldg(h4 + 0), b = __ldg(h4 + 1), c = __ldg(h4 + 2), d = __ldg(h4 + 3);
   if (a.x != bp_fmt::kGlMagic || a.y != 1u) return false;
   const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(a.z);
   const uint64_t total = (uint64_t)c.z | ((uint64_t)c.w << 32);
   if (a.w != g.nblocks || b.x != g.nsuper || b.z != g.off_first || b.w != g.off_sbo ||
       c.x != g.off_bw || c.y != g.off_payload || total != g.off_payload + 4ull * b.y ||
-      total > enc_bytes)
+      total > enc_bytes || d.x > 3u)
     return false;
   v.n = a.z;
+  v.kind = d.x;
   v.nblocks = a.w;
   v.nsuper = b.x;
   v.pw = b.y;

@@ -114,6 +114,47 @@ __device__ __forceinline__ void gl_decode_unit_smem(const GlView &v, const Super
   }
 }
 
+// Kinds DM, D2, D1 (Section 5): the same walk over the superblock, each block
+// decoded by the kind's prefix (from shared memory when staged, else from
+// global memory).
+template <int KIND, bool SUM, class W>
+__device__ __forceinline__ void gl_decode_unit_kind(const GlView &v, const SuperInfo &si,
+                                                    uint32_t q, W words, int lane,
+                                                    uint32_t *__restrict__ out, uint64_t &acc) {
+  for (uint32_t j = 0; j < si.nblk; j++) {
+    const int b = (int)__shfl_sync(kFull, si.b, j);
+    const uint32_t F = __shfl_sync(kFull, si.F, j);
+    const uint32_t woff = __shfl_sync(kFull, si.woff, j);
+    const uint32_t blk = q * 32u + j;
+    uint32_t x[4];
+    gl_block_values_kind<KIND>(b, words(woff), F, lane, x);
+    store_block<SUM>(x, min(128u, v.n - 128u * blk), lane, out + 128ull * blk, acc);
+  }
+}
+
+// Word sources of a block at payload word offset woff.
+struct StageAt {
+  uint32_t sbase, w0;
+  __device__ __forceinline__ SharedWords operator()(uint32_t woff) const {
+    return SharedWords{sbase + 4u * (woff - w0)};
+  }
+};
+struct PayloadAt {
+  const uint32_t *payload;
+  __device__ __forceinline__ GlobalWords operator()(uint32_t woff) const {
+    return GlobalWords{payload + woff};
+  }
+};
+
+template <bool SUM, class W>
+__device__ __forceinline__ void gl_decode_unit_other(const GlView &v, const SuperInfo &si,
+                                                     uint32_t q, W words, int lane,
+                                                     uint32_t *__restrict__ out, uint64_t &acc) {
+  if (v.kind == kDM) gl_decode_unit_kind<kDM, SUM>(v, si, q, words, lane, out, acc);
+  else if (v.kind == kD2) gl_decode_unit_kind<kD2, SUM>(v, si, q, words, lane, out, acc);
+  else gl_decode_unit_kind<kD1, SUM>(v, si, q, words, lane, out, acc);
+}
+
 __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane) {
 #pragma unroll
   for (int dd = 16; dd > 0; dd >>= 1) acc += __shfl_down_sync(kFull, acc, dd);
@@ -123,7 +164,9 @@ __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane
 }
 
 // Unit u belongs to the list with the largest unit_base <= u; the warp keeps
-// the current list's parsed header while consecutive units stay in it.
+// the current list's parsed header while consecutive units stay in it.  This
+// kernel decodes the D4 lists of the call and jumps over the others, which
+// gl_decode_other_kernel decodes (each keeps its own register allocation).
 template <bool SUM>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     gl_decode_kernel(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
@@ -155,6 +198,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
       ok = gl_view(data + L.enc_offset, L.enc_bytes, v) && v.n == L.n;
       if (!ok) {
         if (lane == 0) set_status(status, BP_ERR_CORRUPT);
+      } else if (v.kind != kD4) {  // gl_decode_other_kernel's list: jump over it
+        ok = false;
+        const uint64_t end = base + v.nsuper;
+        if (u < end) u += ((end - u + nwarps - 1) / nwarps - 1) * nwarps;
+        continue;
       } else if (!SUM && L.out_offset + L.n > out_cap) {
         ok = false;
         if (lane == 0) set_status(status, BP_ERR_CAPACITY);
@@ -192,6 +240,59 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   if (SUM && cur != 0xFFFFFFFFu) flush_sum(acc, sums + cur, lane);
 }
 
+// The DM, D2 and D1 lists of the call (Section 5).  CTAs come in groups of
+// `parts` per list; a CTA whose list is D4 (or has a bad header, which the
+// D4 kernel reports) leaves at once, so a call without such lists costs one
+// header read per CTA.  The warps of a list's group share its superblocks.
+template <bool SUM>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    gl_decode_other_kernel(const uint8_t *__restrict__ data, ListSrc src, uint32_t parts,
+                           uint32_t *__restrict__ out, uint64_t out_cap, uint64_t *sums,
+                           uint32_t *status) {
+  const uint32_t li = blockIdx.x / parts, part = blockIdx.x % parts;
+  if (li >= src.count) return;
+  const bp_list L = src.get(li);
+  GlView v;
+  if (!gl_view(data + L.enc_offset, L.enc_bytes, v) || v.n != L.n || v.kind == kD4) return;
+  if (!SUM && L.out_offset + L.n > out_cap) {
+    if (part == 0 && threadIdx.x == 0) set_status(status, BP_ERR_CAPACITY);
+    return;
+  }
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  __shared__ __align__(128) uint8_t s_stage[kThreads / 32][kStageBytes];
+  __shared__ __align__(8) uint64_t s_bar[kThreads / 32];
+  const uint32_t bar = smem_addr(&s_bar[wl]);
+  const uint32_t sbase = smem_addr(&s_stage[wl][0]);
+  uint32_t phase = 0;
+  if (lane == 0) bulk_bar_init(bar);
+  __syncwarp();
+  uint64_t acc = 0;
+  uint32_t *o = out + L.out_offset;
+  const uint32_t step = parts * (kThreads / 32);
+  for (uint32_t q = part * (kThreads / 32) + wl; q < v.nsuper; q += step) {
+    SuperInfo si;
+    if (!gl_super(v, q, lane, si, status)) continue;
+    const uint32_t w0 = __shfl_sync(kFull, si.woff, 0);
+    const uint32_t w1 = __shfl_sync(kFull, si.woff + 4u * si.b, si.nblk - 1);
+    const uint32_t bytes = 4u * (w1 - w0);
+    if (bytes > 0 && bytes <= kStageBytes) {
+      if (lane == 0) bulk_load(bar, sbase, v.payload + w0, bytes);
+      const bool done = bulk_wait(bar, phase);
+      phase ^= 1u;
+      if (!__all_sync(kFull, done)) {  // give up: record it, let the copy land, stop
+        if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
+        bulk_wait(bar, phase ^ 1u);
+        return;
+      }
+      gl_decode_unit_other<SUM>(v, si, q, StageAt{sbase, w0}, lane, o, acc);
+      __syncwarp();
+    } else {
+      gl_decode_unit_other<SUM>(v, si, q, PayloadAt{v.payload}, lane, o, acc);
+    }
+  }
+  if (SUM) flush_sum(acc, sums + li, lane);
+}
+
 template <class K>
 int persistent_grid(K kernel, uint64_t units, int &per_sm_cache) {
   if (per_sm_cache < 0) {
@@ -212,15 +313,25 @@ int launch_gl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
                      uint32_t *out, uint64_t out_cap, uint64_t *sums, uint32_t *status,
                      cudaStream_t s) {
   if (total_units == 0) return BP_OK;
-  static int occ_sum = -1, occ_store = -1;
+  static int occ[4] = {-1, -1, -1, -1};
+  // CTAs per list of the other kinds' kernel: enough to fill the GPU once
+  const uint64_t resident = 8ull * device_sm_count() * kMinBlocks;
+  const uint32_t parts = (uint32_t)std::max<uint64_t>(1, resident / std::max<uint32_t>(src.count, 1u));
+  const uint64_t ogrid64 = (uint64_t)parts * src.count;
+  if (ogrid64 > 0x7FFFFFFFull) return BP_ERR_ARG;
+  const int ogrid = (int)ogrid64;
   if (sums) {
-    const int grid = persistent_grid(gl_decode_kernel<true>, total_units, occ_sum);
+    const int grid = persistent_grid(gl_decode_kernel<true>, total_units, occ[0]);
     gl_decode_kernel<true><<<grid, kThreads, 0, s>>>(data, src, total_units, out, out_cap, sums,
                                                      status);
+    gl_decode_other_kernel<true><<<ogrid, kThreads, 0, s>>>(data, src, parts, out, out_cap,
+                                                            sums, status);
   } else {
-    const int grid = persistent_grid(gl_decode_kernel<false>, total_units, occ_store);
-    gl_decode_kernel<false><<<grid, kThreads, 0, s>>>(data, src, total_units, out, out_cap, sums,
-                                                      status);
+    const int grid = persistent_grid(gl_decode_kernel<false>, total_units, occ[2]);
+    gl_decode_kernel<false><<<grid, kThreads, 0, s>>>(data, src, total_units, out, out_cap,
+                                                      sums, status);
+    gl_decode_other_kernel<false><<<ogrid, kThreads, 0, s>>>(data, src, parts, out, out_cap,
+                                                             sums, status);
   }
   return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
 }

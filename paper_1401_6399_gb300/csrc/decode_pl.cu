@@ -29,6 +29,7 @@
 // Work unit u of a list: its block u - unit_base, then one unit for the tail.
 #include "decode.h"
 #include "bulk.cuh"
+#include "gl_block.cuh"
 #include "pl_block.cuh"
 
 namespace bp {
@@ -75,7 +76,8 @@ struct PlScratch {
   uint64_t *boffw;      // [units] byte offset | width << 56; tail unit: tail offset
   uint32_t *seg_base;   // [count + 1] first segment of each list; [count]: total
   uint32_t *grp_base;   // [count + 1] first group of each list; [count]: total
-  uint32_t *ctl;        // [1] nonzero: the lists do not tile the units, do nothing
+  uint32_t *ctl;        // [0] nonzero: the lists do not tile the units, do nothing;
+                        // [1] nonzero: some list is not D4
   uint32_t *seg_in;     // [segs][kEnt] chain state entering the segment, by group entry
   uint32_t *live;       // [segs][kLiveCap] live line | successor distance << 16
   uint32_t *live_cnt;   // [segs]
@@ -155,7 +157,7 @@ __device__ __forceinline__ uint32_t meta_blocks(const bp_list &L) { return (L.n 
 
 __device__ __forceinline__ bool header_ok(const uint8_t *enc, const bp_list &L) {
   return L.enc_bytes >= 16 && (L.enc_offset & 15u) == 0 && rd_u32(enc) == L.n &&
-         rd_u32(enc + 4) == 0u && rd_u32(enc + 12) == 0u;
+         rd_u32(enc + 4) == 0u && rd_u32(enc + 12) <= 3u;  // word 3: kind of deltas
 }
 
 // Largest i < count with base[i] <= g (the list owning segment or group g).
@@ -183,15 +185,16 @@ __device__ __forceinline__ uint64_t warp_incl_u64(uint64_t v, int lane) {
 }
 
 __global__ void __launch_bounds__(1024)
-    pl_plan(ListSrc src, uint64_t total_units, uint64_t max_s, uint64_t max_g, PlScratch sc,
-            uint32_t *status) {
+    pl_plan(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units, uint64_t max_s,
+            uint64_t max_g, PlScratch sc, uint32_t *status) {
   __shared__ uint64_t s_w[32][3];
   __shared__ uint64_t s_carry[3];
-  __shared__ uint32_t s_bad;
+  __shared__ uint32_t s_bad, s_other;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) {
     s_carry[0] = s_carry[1] = s_carry[2] = 0;
     s_bad = 0;
+    s_other = 0;
   }
   __syncthreads();
   for (uint64_t base = 0; base < src.count; base += 1024) {
@@ -222,6 +225,10 @@ __global__ void __launch_bounds__(1024)
     }
     if (i < src.count) {
       if (L.unit_base != ex[0]) s_bad = 1;
+      // a list of another kind than D4 (header word 3): the decode passes for
+      // those kinds have work
+      if (L.enc_bytes >= 16 && (L.enc_offset & 15u) == 0 && rd_u32(data + L.enc_offset + 12) != 0u)
+        s_other = 1;
       sc.seg_base[i] = (uint32_t)ex[1];
       sc.grp_base[i] = (uint32_t)ex[2];
     }
@@ -239,6 +246,7 @@ __global__ void __launch_bounds__(1024)
     sc.seg_base[src.count] = bad ? 0u : (uint32_t)s_carry[1];
     sc.grp_base[src.count] = bad ? 0u : (uint32_t)s_carry[2];
     sc.ctl[0] = bad ? 1u : 0u;
+    sc.ctl[1] = s_other;
     if (bad) set_status(status, BP_ERR_ARG);
   }
 }
@@ -597,7 +605,32 @@ __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane
 // Blocks j .. j+run-1 of a fully staged chunk, all of width B (pk of lane
 // u: the block's offset in the stage | width << 16).  Column sums, or the
 // decode with the running seed `carry`, stored through `o` or summed into acc.
-template <int B, int MODE>
+// The values before a block, for each kind of Section 5, from the running
+// column sums C_s of the deltas of the list's earlier blocks (lane 8s+c
+// holds C_s in `carry`): D4 x[-4+s] = C_s; DM and D1 x[-1] = C_3 or
+// C_0+C_1+C_2+C_3; D2 x[-2] = C_0+C_2 (even s), x[-1] = C_1+C_3 (odd s).
+template <int KIND>
+__device__ __forceinline__ uint32_t kind_seed(uint32_t carry) {
+  if constexpr (KIND == kDM) return __shfl_sync(kFull, carry, 24);
+  if constexpr (KIND == kD2) return carry + __shfl_xor_sync(kFull, carry, 16);
+  if constexpr (KIND == kD1) {
+    const uint32_t t = carry + __shfl_xor_sync(kFull, carry, 8);
+    return t + __shfl_xor_sync(kFull, t, 16);
+  }
+  return carry;
+}
+
+// The list's last packed value x[128 nb - 1] (what the varint tail follows),
+// from the column sums of all its blocks.
+__device__ __forceinline__ uint32_t kind_last(uint32_t kind, uint32_t carry) {
+  const uint32_t c3 = __shfl_sync(kFull, carry, 24), c1 = __shfl_sync(kFull, carry, 8);
+  const uint32_t c0 = __shfl_sync(kFull, carry, 0), c2 = __shfl_sync(kFull, carry, 16);
+  if (kind == kD2) return c1 + c3;
+  if (kind == kD1) return c0 + c1 + c2 + c3;
+  return c3;  // D4 and DM: position 128 nb - 1 is in column 3
+}
+
+template <int B, int MODE, int KIND>
 __device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run, uint32_t sbase,
                                            int lane, uint32_t &carry, uint32_t *&o,
                                            uint64_t &acc) {
@@ -609,6 +642,21 @@ __device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run
     pl_lane_deltas<B>(PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
     if (MODE == kColsum) {
       carry += d[0] + d[1] + d[2] + d[3];
+      continue;
+    }
+    if constexpr (KIND != kD4) {
+      uint32_t x[4], ctot;
+      prefix_block<KIND>(d, kind_seed<KIND>(carry), lane, x, ctot);
+      carry += ctot;
+      if (MODE == kSum) {
+        acc += (uint64_t)x[0] + x[1] + x[2] + x[3];
+      } else {
+        o[0] = x[0];
+        o[4] = x[1];
+        o[8] = x[2];
+        o[12] = x[3];
+        o += 128;
+      }
       continue;
     }
     const uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
@@ -634,7 +682,7 @@ __device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run
 
 // The 32 blocks of a fully staged chunk, one width dispatch per run of
 // consecutive blocks of equal width.
-template <int MODE>
+template <int MODE, int KIND>
 __device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int lane,
                                              uint32_t &carry, uint32_t *o, uint64_t &acc) {
   const uint32_t bw = pk >> 16;
@@ -645,7 +693,7 @@ __device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int la
     switch (b) {
 #define BP_CASE(B)                                                      \
   case B:                                                               \
-    staged_run<B, MODE>(pk, j, run, sbase, lane, carry, o, acc);        \
+    staged_run<B, MODE, KIND>(pk, j, run, sbase, lane, carry, o, acc);  \
     break;
       BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
       BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
@@ -660,13 +708,26 @@ __device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int la
   }
 }
 
-// Lane l = 8s + c owns column s, rows 4c..4c+3 of each block (positions
-// 16c + 4j + s); `carry` is the running D4 seed of its column.
+// Kind of differential coding of a list (header word 3; lists whose header
+// is bad are marked bad and never decoded).  The column-sum pass needs none.
 template <int MODE>
+__device__ __forceinline__ uint32_t list_kind(const uint8_t *data, const bp_list &L) {
+  if (MODE == kColsum || L.enc_bytes < 16) return kD4;
+  const uint32_t k = rd_u32(data + L.enc_offset + 12);
+  return k <= 3u ? k : kD4;
+}
+
+// Lane l = 8s + c owns column s, rows 4c..4c+3 of each block (positions
+// 16c + 4j + s); `carry` is the running column sum C_s of the deltas of the
+// list's earlier blocks, from which each kind's seed follows (kind_seed).
+// The decode passes come in two kernels: OTHER = false decodes the D4 lists
+// and passes over the rest, OTHER = true the DM, D2 and D1 lists (each keeps
+// a register allocation of its own); the column-sum pass takes every kind.
+template <int MODE, bool OTHER = false>
 __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
     pl_units(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
              uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t *status) {
-  if (sc.ctl[0]) return;
+  if (sc.ctl[0] || (OTHER && !sc.ctl[1])) return;
   const int lane = threadIdx.x & 31, s = lane >> 3, c = lane & 7;
   const uint64_t warp = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kThreads) >> 5;
@@ -687,6 +748,9 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
     uint32_t li = src.find(u0);
     bp_list L = src.get(li);
     uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+    uint32_t kind = list_kind<MODE>(data, L);
+    // a chunk of one list of the other kernel's kind: nothing to do here
+    if (MODE != kColsum && u0 + cnt <= nxt && (kind != kD4) != OTHER) continue;
     // The chunk's leading blocks of list li (lanes [0, m)) lie back to back in
     // the meta-block region, 16-byte aligned, only width lines between them:
     // stage them in shared memory with one bulk copy when they fit.
@@ -697,6 +761,7 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
       uint64_t m = nb0 > k0 ? nb0 - k0 : 0;
       if (m > cnt) m = cnt;
       if (m > nxt - u0) m = nxt - u0;
+      if (MODE != kColsum && (kind != kD4) != OTHER) m = 0;  // not this kernel's list
       const uint64_t offl = eL & kOffMask;
       const uint32_t bl = (uint32_t)(eL >> 56);
       const bool fit = __all_sync(kFull, (uint32_t)lane >= m || (bl <= 32u && (offl & 15u) == 0));
@@ -733,9 +798,14 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
         if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
         acc_list = li;
       }
-      staged_chunk<MODE>(pk, sbase, lane, carry,
-                         MODE == kStore ? out + L.out_offset + 128ull * k0 + 16 * c + s : nullptr,
-                         acc);
+      uint32_t *o = MODE == kStore ? out + L.out_offset + 128ull * k0 + 16 * c + s : nullptr;
+      if constexpr (MODE == kColsum || !OTHER) {
+        staged_chunk<MODE, kD4>(pk, sbase, lane, carry, o, acc);
+      } else {
+        if (kind == kDM) staged_chunk<MODE, kDM>(pk, sbase, lane, carry, o, acc);
+        else if (kind == kD2) staged_chunk<MODE, kD2>(pk, sbase, lane, carry, o, acc);
+        else staged_chunk<MODE, kD1>(pk, sbase, lane, carry, o, acc);
+      }
       __syncwarp();  // every lane is done with the stage before it is refilled
       if (MODE == kColsum) {
         carry += __shfl_xor_sync(kFull, carry, 1);
@@ -756,15 +826,20 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
         li++;
         L = src.get(li);
         nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+        kind = list_kind<MODE>(data, L);
       }
       const uint64_t k = u - L.unit_base;
       if (k == 0) {
         carry = 0;
         head = true;
       }
+      if (MODE != kColsum && (kind != kD4) != OTHER) continue;  // the other kernel's list
       const uint64_t e = __shfl_sync(kFull, eL, j);
-      if (k >= L.n / 128u) {  // the tail unit: column 3 holds the last packed value
-        if (MODE != kColsum && lane == 24) sc.lastval[li] = carry;
+      if (k >= L.n / 128u) {  // the tail unit: record the last packed value
+        if (MODE != kColsum) {
+          const uint32_t lv = kind_last(kind, carry);
+          if (lane == 24) sc.lastval[li] = lv;
+        }
         continue;
       }
       const uint32_t b = (uint32_t)(e >> 56);
@@ -781,19 +856,35 @@ __global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
         carry += d[0] + d[1] + d[2] + d[3];
         continue;
       }
-      uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
-      uint32_t inc = x3;
+      uint32_t x0, x1, x2, x3;
+      if constexpr (!OTHER) {
+        x0 = d[0];
+        x1 = x0 + d[1];
+        x2 = x1 + d[2];
+        x3 = x2 + d[3];
+        uint32_t inc = x3;
 #pragma unroll
-      for (int dd = 1; dd < 8; dd <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
-        if (c >= dd) inc += t;
+        for (int dd = 1; dd < 8; dd <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+          if (c >= dd) inc += t;
+        }
+        const uint32_t base = carry + inc - x3;
+        x0 += base;
+        x1 += base;
+        x2 += base;
+        x3 += base;
+        carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
+      } else {
+        uint32_t x[4], ctot;
+        if (kind == kDM) prefix_block<kDM>(d, kind_seed<kDM>(carry), lane, x, ctot);
+        else if (kind == kD2) prefix_block<kD2>(d, kind_seed<kD2>(carry), lane, x, ctot);
+        else prefix_block<kD1>(d, kind_seed<kD1>(carry), lane, x, ctot);
+        carry += ctot;
+        x0 = x[0];
+        x1 = x[1];
+        x2 = x[2];
+        x3 = x[3];
       }
-      const uint32_t base = carry + inc - x3;
-      x0 += base;
-      x1 += base;
-      x2 += base;
-      x3 += base;
-      carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
       if (MODE == kSum) {
         if (acc_list != li) {
           if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
@@ -1033,7 +1124,7 @@ int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
   };
   const int lgrid = (int)std::min<uint64_t>((src.count + 7) / 8, 4096);
   if (cudaMemsetAsync(sc.boffw, 0xFF, 8 * total_units, s) != cudaSuccess) return BP_ERR_CUDA;
-  pl_plan<<<1, 1024, 0, s>>>(src, total_units, S, G, sc, status);
+  pl_plan<<<1, 1024, 0, s>>>(data, src, total_units, S, G, sc, status);
   pl_parse<<<8 * sms, kThreads, 0, s>>>(data, src, sc);
   pl_resolve<<<(int)std::min<uint64_t>(src.count, 4ull * sms), kThreads, 0, s>>>(data, src, sc,
                                                                                    status);
@@ -1044,13 +1135,18 @@ int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
   pl_scan_reduce<<<(unsigned)ntiles, kThreads, 0, s>>>(nch, sc);
   pl_scan_top<<<1, 1024, 0, s>>>(ntiles, sc);
   pl_scan_down<<<(unsigned)ntiles, kThreads, 0, s>>>(nch, sc);
+  static int occ_sum_k = -1, occ_store_k = -1;
   if (sums) {
     pl_units<kSum><<<unit_grid(resident_grid(pl_units<kSum>, occ_sum)), kThreads, 0, s>>>(
         data, src, total_units, out, sums, sc, status);
+    pl_units<kSum, true><<<unit_grid(resident_grid(pl_units<kSum, true>, occ_sum_k)), kThreads,
+                           0, s>>>(data, src, total_units, out, sums, sc, status);
     pl_tail<true><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   } else {
     pl_units<kStore><<<unit_grid(resident_grid(pl_units<kStore>, occ_store)), kThreads, 0, s>>>(
         data, src, total_units, out, sums, sc, status);
+    pl_units<kStore, true><<<unit_grid(resident_grid(pl_units<kStore, true>, occ_store_k)),
+                             kThreads, 0, s>>>(data, src, total_units, out, sums, sc, status);
     pl_tail<false><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   }
   return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;

@@ -83,6 +83,140 @@ __device__ __forceinline__ void gl_lane_values(const L &ld, uint32_t F, int lane
   for (int j = 0; j < 4; j++) x[j] += base;
 }
 
+// ---- the other kinds of differential coding of Section 5 -----------------
+//
+// prefix_block<KIND> turns the four deltas d[j] of lane l = 8s + c (block
+// positions 16c + 4j + s) into values, given the values before the block:
+// s0 is x[-4+s] for D4 (the lane's column), x[-1] for DM and D1, and
+// x[-2] (even s) or x[-1] (odd s) for D2; a GL block passes its first value
+// F for all of them.  ctot receives the sum of the lane's column of deltas
+// over the whole block (what a carried seed needs).
+//   D4: a running sum down the column (per lane, then a 3-step scan over
+//       the 8 lanes of the column).
+//   DM: row t adds x[4t-1], the last value of row t-1, which is the D4-style
+//       running value of column 3: 4 shuffles from the column-3 lanes.
+//   D2: columns 0/2 and 1/3 form two chains; pair sums (one shuffle per row)
+//       run down the rows, column 0 (1) takes the chain before its row plus
+//       its own delta, column 2 (3) the chain through its row.
+//   D1: an inclusive sum across the row (2 shuffles per row), the row totals
+//       run down the rows.
+enum { kD4 = 0, kDM = 1, kD2 = 2, kD1 = 3 };
+
+// Exclusive sum of v over the lanes 8s .. 8s+c-1 of the lane's column.
+__device__ __forceinline__ uint32_t col_excl(uint32_t v, int lane) {
+  const int c = lane & 7;
+  uint32_t inc = v;
+#pragma unroll
+  for (int dd = 1; dd < 8; dd <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+    if (c >= dd) inc += t;
+  }
+  return inc - v;
+}
+
+template <int KIND>
+__device__ __forceinline__ void prefix_block(const uint32_t d[4], uint32_t s0, int lane,
+                                             uint32_t x[4], uint32_t &ctot) {
+  const int s = lane >> 3, c = lane & 7;
+  if constexpr (KIND == kD4 || KIND == kDM) {
+    uint32_t run[4];
+    run[0] = d[0];
+    run[1] = run[0] + d[1];
+    run[2] = run[1] + d[2];
+    run[3] = run[2] + d[3];
+    const uint32_t e = col_excl(run[3], lane);
+    ctot = __shfl_sync(kFull, e + run[3], (lane & ~7) | 7);
+    uint32_t y[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) y[j] = s0 + e + run[j];
+    if constexpr (KIND == kD4) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) x[j] = y[j];
+    } else {
+      // y of the column-3 lanes: x[4t+3]; row t's base is x[4t-1]
+      const uint32_t p3 = __shfl_sync(kFull, y[3], 24 + ((c + 7) & 7));  // lane (3, c-1)
+      const uint32_t b0 = c ? p3 : s0;
+      const uint32_t b1 = __shfl_sync(kFull, y[0], 24 + c);
+      const uint32_t b2 = __shfl_sync(kFull, y[1], 24 + c);
+      const uint32_t b3 = __shfl_sync(kFull, y[2], 24 + c);
+      x[0] = d[0] + b0;
+      x[1] = d[1] + b1;
+      x[2] = d[2] + b2;
+      x[3] = d[3] + b3;
+    }
+  } else if constexpr (KIND == kD2) {
+    uint32_t rp[4], rp_prev[4], acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const uint32_t pj = d[j] + __shfl_xor_sync(kFull, d[j], 16);  // columns s and s^2
+      rp_prev[j] = acc;
+      acc += pj;
+      rp[j] = acc;
+    }
+    const uint32_t e = col_excl(rp[3], lane);
+#pragma unroll
+    for (int j = 0; j < 4; j++) x[j] = s >= 2 ? s0 + e + rp[j] : s0 + e + rp_prev[j] + d[j];
+    uint32_t t = d[0] + d[1] + d[2] + d[3];
+    t += __shfl_xor_sync(kFull, t, 1);
+    t += __shfl_xor_sync(kFull, t, 2);
+    t += __shfl_xor_sync(kFull, t, 4);
+    ctot = t;
+  } else {  // kD1
+    uint32_t q[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {  // inclusive sum over s of row 4c+j
+      uint32_t v = d[j];
+      uint32_t t = __shfl_up_sync(kFull, v, 8);
+      if (s >= 1) v += t;
+      t = __shfl_up_sync(kFull, v, 16);
+      if (s >= 2) v += t;
+      q[j] = v;
+    }
+    uint32_t rr_prev[4], acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      rr_prev[j] = acc;
+      acc += __shfl_sync(kFull, q[j], 24 + c);  // the row's total
+    }
+    const uint32_t e = col_excl(acc, lane);
+#pragma unroll
+    for (int j = 0; j < 4; j++) x[j] = s0 + e + rr_prev[j] + q[j];
+    uint32_t t = d[0] + d[1] + d[2] + d[3];
+    t += __shfl_xor_sync(kFull, t, 1);
+    t += __shfl_xor_sync(kFull, t, 2);
+    t += __shfl_xor_sync(kFull, t, 4);
+    ctot = t;
+  }
+}
+
+// Values of a GL block of width B and kind KIND (all seeds F).
+template <int B, int KIND, class L>
+__device__ __forceinline__ void gl_lane_values_kind(const L &ld, uint32_t F, int lane,
+                                                    uint32_t x[4]) {
+  uint32_t d[4], ctot;
+  gl_lane_deltas<B>(ld, lane, d);
+  prefix_block<KIND>(d, F, lane, x, ctot);
+}
+
+template <int KIND, class L>
+__device__ __forceinline__ void gl_block_values_kind(int b, const L &ld, uint32_t F, int lane,
+                                                     uint32_t x[4]) {
+  switch (b) {
+#define BP_CASE(B) \
+  case B:          \
+    gl_lane_values_kind<B, KIND>(ld, F, lane, x); \
+    break;
+    BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
+    BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
+    BP_CASE(14) BP_CASE(15) BP_CASE(16) BP_CASE(17) BP_CASE(18) BP_CASE(19) BP_CASE(20)
+    BP_CASE(21) BP_CASE(22) BP_CASE(23) BP_CASE(24) BP_CASE(25) BP_CASE(26) BP_CASE(27)
+    BP_CASE(28) BP_CASE(29) BP_CASE(30) BP_CASE(31) BP_CASE(32)
+#undef BP_CASE
+    default:
+      x[0] = x[1] = x[2] = x[3] = 0u;
+  }
+}
+
 // Runtime-width dispatch (b is warp-uniform, so the switch never diverges).
 template <class L>
 __device__ __forceinline__ void gl_block_values_from(int b, const L &ld, uint32_t F, int lane,

@@ -50,9 +50,13 @@ __global__ void __launch_bounds__(kIxThreads)
   uint32_t *s_f = s_r + kPairGroups * 128;
 
   GlView R, F;
-  const bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
-  const bool okF = gl_view(a.f_enc, a.f_bytes, F) && F.n == a.nf;
+  bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
+  bool okF = gl_view(a.f_enc, a.f_bytes, F) && F.n == a.nf;
   if ((!okR || !okF) && threadIdx.x == 0 && t == 0) set_status(to.status, BP_ERR_CORRUPT);
+  if (okR && okF && (R.kind != 0u || F.kind != 0u)) {  // the probes need D4 columns
+    if (threadIdx.x == 0 && t == 0) set_status(to.status, BP_ERR_ARG);
+    okR = okF = false;
+  }
 
   uint32_t scount = 0;
   const uint64_t p0 = ((uint64_t)t * kIxWarps + w) * vpw;  // first r position of this warp

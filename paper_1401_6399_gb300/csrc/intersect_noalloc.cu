@@ -76,9 +76,13 @@ __global__ void __launch_bounds__(kIxThreads)
   const uint32_t t = s_tile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   GlView R, F;
-  const bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
-  const bool okF = gl_view(a.f_enc, a.f_bytes, F) && F.n == a.nf;
+  bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
+  bool okF = gl_view(a.f_enc, a.f_bytes, F) && F.n == a.nf;
   if ((!okR || !okF) && threadIdx.x == 0 && t == 0) set_status(to.status, BP_ERR_CORRUPT);
+  if (okR && okF && (R.kind != 0u || F.kind != 0u)) {  // the probes need D4 columns
+    if (threadIdx.x == 0 && t == 0) set_status(to.status, BP_ERR_ARG);
+    okR = okF = false;
+  }
   uint32_t v[4] = {0, 0, 0, 0};
   bool valid[4] = {false, false, false, false}, hit[4] = {false, false, false, false};
   const uint32_t kb = t * kIxWarps + w;

@@ -172,10 +172,13 @@ __global__ void __launch_bounds__(1024) scan_u32_kernel(uint32_t *a, uint32_t n)
 
 // ---- 3. the persistent fused kernel --------------------------------------------------------
 
-__device__ __forceinline__ bool term_view(const uint8_t *data, const bp_list *lists, uint32_t t,
-                                          GlView &v) {
+// 0, or the status of a term whose list cannot be used: BP_ERR_CORRUPT, or
+// BP_ERR_ARG for a list that is not D4 (the probes need D4 columns).
+__device__ __forceinline__ uint32_t term_view(const uint8_t *data, const bp_list *lists,
+                                              uint32_t t, GlView &v) {
   const bp_list L = lists[t];
-  return gl_view(data + L.enc_offset, L.enc_bytes, v) && v.n == L.n;
+  if (!gl_view(data + L.enc_offset, L.enc_bytes, v) || v.n != L.n) return BP_ERR_CORRUPT;
+  return v.kind == 0u ? 0u : (uint32_t)BP_ERR_ARG;
 }
 
 // At most 80 registers: 3 CTAs of 8 warps (or 6 of 4) per SM; more warps
@@ -206,7 +209,8 @@ __global__ void __launch_bounds__(256, 3)
     const uint32_t k = (uint32_t)(toff[q + 1] - tb);
     GlView V1;
     uint32_t scount = 0;
-    if (term_view(data, lists, sc.sorted[tb], V1)) {
+    const uint32_t tv = term_view(data, lists, sc.sorted[tb], V1);
+    if (tv == 0u) {
       // the item's blocks of the shortest list; bit 4g+j of `alive`: value
       // 32j + lane of block g is still a candidate
       const uint32_t b0 = c * chunk, b1 = min(V1.nblocks, b0 + chunk);
@@ -223,8 +227,9 @@ __global__ void __launch_bounds__(256, 3)
       // list searched run by run with its dense window moving forward
       for (uint32_t t = 1; t < k && __any_sync(kFull, alive != 0u); t++) {
         GlView F;
-        if (!term_view(data, lists, sc.sorted[tb + t], F)) {
-          if (lane == 0) set_status(status, BP_ERR_CORRUPT);
+        const uint32_t tf = term_view(data, lists, sc.sorted[tb + t], F);
+        if (tf != 0u) {
+          if (lane == 0) set_status(status, tf);
           alive = 0;
           break;
         }
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(256, 3)
         }
       }
     } else if (lane == 0) {
-      set_status(status, BP_ERR_CORRUPT);
+      set_status(status, tv);
     }
     __syncwarp();
     uint64_t off = 0;

@@ -129,6 +129,43 @@ def test_decode_batch(orc, layout):
     assert sums.tolist() == [int(x.astype(np.uint64).sum()) for x in xs]
 
 
+KINDS = [1, 2, 3]  # DM, D2, D1 (Section 5); D4 is every other test here
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("kind", KINDS)
+def test_decode_kinds(orc, layout, kind):
+    """DM, D2 and D1 streams decode bit-exactly (both layouts): edge lengths,
+    ragged tails, widths from 1 to 32 and every width dispatch path."""
+    rng = np.random.default_rng(10 * kind + layout)
+    for n in (0, 1, 5, 127, 128, 129, 2047, 2049, 4097, 3 * 2048 + 15 * 128 + 127, 300_001):
+        for U in (n + 1, 64 * n + 64, 1 << 32):
+            x = np.sort(rng.choice(U, n, replace=False)).astype(np.uint32)
+            enc = capi.bp_encode(x, layout, delta=kind)
+            want = orc.pl_decode(enc.tobytes()) if layout == 0 else orc.gl_decode(enc.tobytes())
+            assert np.array_equal(want, x)
+            got = api.as_u32(api.decode(api.to_device(enc), layout, x.size))
+            assert np.array_equal(got, want), (layout, kind, n, U)
+            assert api.decode_sum(api.to_device(enc), layout, x.size) == int(x.astype(np.uint64).sum()) % (1 << 64)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_decode_batch_mixed_kinds(orc, layout):
+    """One batch of lists of all four kinds, clustered and uniform: every
+    list decodes with its own kind (read from its header)."""
+    xs, encs = [], []
+    for i in range(12):
+        n = [70_000, 128 * 40 + 3, 2048 * 5, 99][i % 4]
+        x = (W.clustered(n, 0, 1 << 30, 7000 + i) if i % 2 else
+             W.uniform(n, 0, 1 << 30, 7000 + i))
+        xs.append(x)
+        encs.append(capi.bp_encode(x, layout, delta=i % 4))
+    batch = api.ListBatch(encs, [x.size for x in xs], layout)
+    got = api.as_u32(batch.decode())
+    assert np.array_equal(got, np.concatenate(xs))
+    assert batch.sums().tolist() == [int(x.astype(np.uint64).sum()) for x in xs]
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_decode_batch_host(orc, layout):
     """bp_decode_batch_host from pinned host memory to pinned host memory.

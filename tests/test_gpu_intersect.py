@@ -127,3 +127,23 @@ def test_capacity_overflow_reports_count():
     assert int(st.item()) == capi.BP_ERR_CAPACITY
     assert int(cnt.item()) == x.size
     assert np.array_equal(api.as_u32(out), x[:100])
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_kinds_unfused_and_fused_rejection(orc, kind):
+    """Lists coded with DM, D2 or D1 (Section 5): the unfused intersection
+    (decode both, then intersect) is exact in both layouts; the fused path,
+    whose probes use D4 columns, records BP_ERR_ARG instead of an answer."""
+    f = W.uniform(1 << 18, 0, 1 << 22, 0x7100 + kind)
+    r = W.pair_short(f, 1 << 12, 400, 1 << 22, 0x7200 + kind)
+    want = orc.intersect(r, f)
+    for layout in (capi.BP_LAYOUT_PAPER, capi.BP_LAYOUT_GPU):
+        er = api.to_device(capi.bp_encode(r, layout, delta=kind))
+        ef = api.to_device(capi.bp_encode(f, layout, delta=kind))
+        got = api.intersect_pair(er, r.size, ef, f.size, layout, capi.BP_MODE_UNFUSED)
+        assert np.array_equal(api.as_u32(got), want), (kind, layout)
+    er = api.to_device(capi.bp_encode(r, capi.BP_LAYOUT_GPU, delta=kind))
+    ef = api.to_device(capi.bp_encode(f, capi.BP_LAYOUT_GPU, delta=kind))
+    with pytest.raises(capi.BPError) as e:
+        api.intersect_pair(er, r.size, ef, f.size, capi.BP_LAYOUT_GPU, capi.BP_MODE_FUSED)
+    assert e.value.code == capi.BP_ERR_ARG
