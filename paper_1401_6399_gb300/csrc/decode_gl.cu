@@ -315,7 +315,7 @@ int launch_gl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
   if (total_units == 0) return BP_OK;
   static int occ[4] = {-1, -1, -1, -1};
   // CTAs per list of the other kinds' kernel: enough to fill the GPU once
-  const uint64_t resident = 8ull * device_sm_count() * kMinBlocks;
+  const uint64_t resident = (uint64_t)device_sm_count() * kMinBlocks;
   const uint32_t parts = (uint32_t)std::max<uint64_t>(1, resident / std::max<uint32_t>(src.count, 1u));
   const uint64_t ogrid64 = (uint64_t)parts * src.count;
   if (ogrid64 > 0x7FFFFFFFull) return BP_ERR_ARG;
