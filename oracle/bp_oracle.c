@@ -330,7 +330,7 @@ int orc_stream_count(const uint8_t *in, size_t nbytes, size_t *n_out) {
     *n_out = rd32(in);
     return ORC_OK;
   }
-  if (nbytes >= 64 && rd32(in + 4) == 1u) {
+  if (nbytes >= 64 && (rd32(in + 4) == 1u || rd32(in + 4) == 3u)) {
     *n_out = rd32(in + 8);
     return ORC_OK;
   }
@@ -602,6 +602,252 @@ int orc_gl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
       wpos += 4 * (size_t)b;
     }
     if (rc == ORC_OK && rd32(sbo + 4 * (sb + 1)) != wpos) rc = ORC_ECORRUPT;
+  }
+  free(payload);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* S4-FastPFOR (Section 4.4, Fig. 3) in a GPU layout (GP).  Not the        */
+/* paper's byte format: blocks of 128 deltas (any kind of Section 5, each  */
+/* block restarting from its first value F as in GL) are bit packed at a   */
+/* width b' <= b, the deltas >= 2^b' are exceptions whose positions (one   */
+/* byte each) and b - b' high bits are stored per page of 32 blocks.       */
+/*                                                                          */
+/* header, 16 little-endian u32 words:                                      */
+/*   0 magic 0x34504742   1 layout tag 3     2 n          3 nblocks        */
+/*   4 npages             5 payload words    6 off_first  7 off_spo        */
+/*   8 off_meta           9 off_payload     10 total bytes (low)           */
+/*  11 total bytes (high) 12 kind            13..15 zero                   */
+/* sections, each starting on a 16-byte boundary:                           */
+/*   first[nblocks] u32, spo[npages+1] u32 (payload word offset of every   */
+/*   page, then the total), meta[nblocks] of 4 bytes {b', b - b', c, 0}    */
+/*   (c = number of exceptions), payload words.                             */
+/* page p (blocks 32p ..): the low b' bits of every block, 4 b' words per   */
+/*   block in GL's column order; then the exception positions, c bytes per  */
+/*   block in ascending order, zero-padded to a word; then the high bits,   */
+/*   b - b' per exception, blocks and exceptions in order, least           */
+/*   significant bit first, zero-padded to a word; then zero words to a     */
+/*   multiple of 4.                                                         */
+/* ------------------------------------------------------------------------ */
+
+#define GP_MAGIC 0x34504742u
+
+static void gp_offsets(size_t nblocks, size_t npages, size_t *off_first,
+                       size_t *off_spo, size_t *off_meta, size_t *off_payload) {
+  *off_first = 64;
+  *off_spo = *off_first + up16(4 * nblocks);
+  *off_meta = *off_spo + up16(4 * (npages + 1));
+  *off_payload = *off_meta + up16(4 * nblocks);
+}
+
+size_t orc_gp_bound(size_t n) {
+  size_t nb = (n + 127) / 128, np = (nb + 31) / 32;
+  size_t a, b, c, p;
+  gp_offsets(nb, np, &a, &b, &c, &p);
+  /* a block never costs more bits than at b' = b (128 b <= 4096); a page
+   * adds less than 5 words of padding (positions, high bits, 4-word end) */
+  return p + nb * 512 + np * 32;
+}
+
+/* Section 4.4: b is the width of the largest delta; b' in [0, b] minimizes
+ * 128 b' + c(b') (b - b' + 8), c(b') = number of deltas >= 2^b'.  Where
+ * several b' tie, the largest is taken (fewer exceptions; the paper does
+ * not say). */
+void orc_pfor_choose(const uint32_t d[128], unsigned *b_out, unsigned *bp_out,
+                     unsigned *c_out) {
+  const unsigned b = orc_max_bits(d, 128);
+  unsigned best = b, best_c = 0;
+  uint64_t best_cost = 128ull * b;
+  for (unsigned bp = 0; bp < b; bp++) {
+    unsigned c = 0;
+    for (unsigned i = 0; i < 128; i++)
+      if (orc_bits(d[i]) > bp) c++;
+    const uint64_t cost = 128ull * bp + (uint64_t)c * (b - bp + 8);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = bp;
+      best_c = c;
+    }
+  }
+  /* ties: a later (larger) b' with the same cost wins */
+  for (unsigned bp = best + 1; bp <= b; bp++) {
+    unsigned c = 0;
+    for (unsigned i = 0; i < 128; i++)
+      if (orc_bits(d[i]) > bp) c++;
+    if (128ull * bp + (uint64_t)c * (b - bp + 8) == best_cost) {
+      best = bp;
+      best_c = c;
+    }
+  }
+  *b_out = b;
+  *bp_out = best;
+  *c_out = best_c;
+}
+
+int orc_gp_encode_kind(const uint32_t *x, size_t n, int kind, uint8_t *out,
+                       size_t cap, size_t *out_bytes) {
+  if ((!x && n) || !out || !out_bytes) return ORC_EARG;
+  if (kind < ORC_DELTA_D4 || kind > ORC_DELTA_D1) return ORC_EARG;
+  if (n > 0x7FFFFFFFull) return ORC_EARG;
+  if (!is_sorted_distinct(x, n)) return ORC_EARG;
+  if (cap < orc_gp_bound(n)) return ORC_ECAPACITY;
+
+  const size_t nb = (n + 127) / 128, np = (nb + 31) / 32;
+  size_t off_first, off_spo, off_meta, off_payload;
+  gp_offsets(nb, np, &off_first, &off_spo, &off_meta, &off_payload);
+  memset(out, 0, cap);
+
+  size_t wpos = 0; /* payload word offset */
+  uint32_t d[128];
+  for (size_t p = 0; p < np; p++) {
+    wr32(out + off_spo + 4 * p, (uint32_t)wpos);
+    const size_t k0 = 32 * p, k1 = (k0 + 32 < nb) ? k0 + 32 : nb;
+    /* pass over the page's blocks: low bits, then collect the exceptions */
+    uint8_t pos[32 * 128];
+    uint32_t high[32 * 128];
+    unsigned hw[32 * 128];
+    size_t ne = 0;
+    for (size_t k = k0; k < k1; k++) {
+      const unsigned cnt = (unsigned)((n - 128 * k) < 128 ? (n - 128 * k) : 128);
+      gl_block_deltas(x + 128 * k, cnt, kind, d);
+      unsigned b, bp, c;
+      orc_pfor_choose(d, &b, &bp, &c);
+      wr32(out + off_first + 4 * k, x[128 * k]);
+      out[off_meta + 4 * k + 0] = (uint8_t)bp;
+      out[off_meta + 4 * k + 1] = (uint8_t)(b - bp);
+      out[off_meta + 4 * k + 2] = (uint8_t)c;
+      uint32_t words[128];
+      for (unsigned q = 0; q < 4 * bp; q++) words[q] = 0;
+      for (unsigned t = 0; t < 32; t++)
+        for (unsigned s = 0; s < 4; s++)
+          put_bits(words, (size_t)bp * (32 * s + t), d[4 * t + s] & low_mask(bp), bp);
+      for (unsigned q = 0; q < 4 * bp; q++)
+        wr32(out + off_payload + 4 * (wpos + q), words[q]);
+      wpos += 4 * bp;
+      for (unsigned i = 0; i < 128; i++)
+        if (orc_bits(d[i]) > bp) {
+          pos[ne] = (uint8_t)i;
+          high[ne] = d[i] >> bp; /* bp < b <= 32 here */
+          hw[ne] = b - bp;
+          ne++;
+        }
+    }
+    for (size_t e = 0; e < ne; e++) out[off_payload + 4 * wpos + e] = pos[e];
+    wpos += (ne + 3) / 4;
+    size_t hbits = 0;
+    for (size_t e = 0; e < ne; e++) hbits += hw[e];
+    uint32_t *hwords = (uint32_t *)calloc((hbits + 31) / 32 + 1, sizeof(uint32_t));
+    if (!hwords) return ORC_EARG;
+    size_t bit = 0;
+    for (size_t e = 0; e < ne; e++) {
+      put_bits(hwords, bit, high[e], hw[e]);
+      bit += hw[e];
+    }
+    for (size_t q = 0; q < (hbits + 31) / 32; q++)
+      wr32(out + off_payload + 4 * (wpos + q), hwords[q]);
+    free(hwords);
+    wpos += (hbits + 31) / 32;
+    wpos = (wpos + 3) & ~(size_t)3;
+  }
+  wr32(out + off_spo + 4 * np, (uint32_t)wpos);
+  const size_t total = off_payload + 4 * wpos;
+  const uint32_t hdr[16] = {GP_MAGIC,
+                            3u,
+                            (uint32_t)n,
+                            (uint32_t)nb,
+                            (uint32_t)np,
+                            (uint32_t)wpos,
+                            (uint32_t)off_first,
+                            (uint32_t)off_spo,
+                            (uint32_t)off_meta,
+                            (uint32_t)off_payload,
+                            (uint32_t)(total & 0xFFFFFFFFu),
+                            (uint32_t)((uint64_t)total >> 32),
+                            (uint32_t)kind,
+                            0,
+                            0,
+                            0};
+  for (int i = 0; i < 16; i++) wr32(out + 4 * i, hdr[i]);
+  *out_bytes = total;
+  return ORC_OK;
+}
+
+int orc_gp_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
+                  size_t *n_out) {
+  if (!in || !n_out) return ORC_EARG;
+  if (nbytes < 64) return ORC_ECORRUPT;
+  if (rd32(in) != GP_MAGIC || rd32(in + 4) != 3u) return ORC_ECORRUPT;
+  const size_t n = rd32(in + 8), nb = rd32(in + 12), np = rd32(in + 16);
+  const size_t pw = rd32(in + 20);
+  const uint32_t kind = rd32(in + 48);
+  if (nb != (n + 127) / 128 || np != (nb + 31) / 32 || kind > ORC_DELTA_D1)
+    return ORC_ECORRUPT;
+  size_t off_first, off_spo, off_meta, off_payload;
+  gp_offsets(nb, np, &off_first, &off_spo, &off_meta, &off_payload);
+  if (rd32(in + 24) != off_first || rd32(in + 28) != off_spo ||
+      rd32(in + 32) != off_meta || rd32(in + 36) != off_payload)
+    return ORC_ECORRUPT;
+  const uint64_t total = (uint64_t)rd32(in + 40) | ((uint64_t)rd32(in + 44) << 32);
+  if (total != off_payload + 4 * pw || total > nbytes) return ORC_ECORRUPT;
+  *n_out = n;
+  if (n > cap) return ORC_ECAPACITY;
+  if (n && !out) return ORC_EARG;
+
+  uint32_t *payload = (uint32_t *)malloc((pw + 1) * sizeof(uint32_t));
+  if (!payload) return ORC_EARG;
+  for (size_t q = 0; q < pw; q++) payload[q] = rd32(in + off_payload + 4 * q);
+  payload[pw] = 0;
+  int rc = ORC_OK;
+  for (size_t p = 0; p < np && rc == ORC_OK; p++) {
+    const size_t k0 = 32 * p, k1 = (k0 + 32 < nb) ? k0 + 32 : nb;
+    const size_t page = rd32(in + off_spo + 4 * p), page_end = rd32(in + off_spo + 4 * (p + 1));
+    /* where the page's positions and high bits start */
+    size_t low = 0, ne = 0, hbits = 0;
+    for (size_t k = k0; k < k1; k++) {
+      const unsigned bp = in[off_meta + 4 * k], w = in[off_meta + 4 * k + 1];
+      const unsigned c = in[off_meta + 4 * k + 2];
+      if (bp + w > 32 || (w == 0) != (c == 0) || c > 128) {
+        rc = ORC_ECORRUPT;
+        break;
+      }
+      low += 4 * bp;
+      ne += c;
+      hbits += (size_t)c * w;
+    }
+    const size_t pos_w = page + low, high_w = pos_w + (ne + 3) / 4;
+    const size_t end = (high_w + (hbits + 31) / 32 + 3) & ~(size_t)3;
+    if (rc || end != page_end || page_end > pw) {
+      rc = ORC_ECORRUPT;
+      break;
+    }
+    const uint8_t *posb = in + off_payload + 4 * pos_w;
+    size_t wpos = page, e = 0, bit = 0;
+    for (size_t k = k0; k < k1; k++) {
+      const unsigned bp = in[off_meta + 4 * k], w = in[off_meta + 4 * k + 1];
+      const unsigned c = in[off_meta + 4 * k + 2];
+      uint32_t d[128];
+      /* unpack b' bits, patch the exceptions, then the prefix (Section 4.4:
+       * unpacking, patching and the prefix sum in that order) */
+      for (unsigned t = 0; t < 32; t++)
+        for (unsigned s = 0; s < 4; s++)
+          d[4 * t + s] = get_bits(payload + wpos, (size_t)bp * (32 * s + t), bp);
+      for (unsigned i = 0; i < c; i++, e++) {
+        const unsigned q = posb[e];
+        if (q > 127) {
+          rc = ORC_ECORRUPT;
+          break;
+        }
+        d[q] |= get_bits(payload + high_w, bit, w) << bp;
+        bit += w;
+      }
+      if (rc) break;
+      uint32_t x[128];
+      orc_prefix((int)kind, d, 128, rd32(in + off_first + 4 * k), x);
+      const size_t cnt = (n - 128 * k) < 128 ? (n - 128 * k) : 128;
+      for (size_t i = 0; i < cnt; i++) out[128 * k + i] = x[i];
+      wpos += 4 * (size_t)bp;
+    }
   }
   free(payload);
   return rc;

@@ -128,6 +128,22 @@ int orc_gl_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
  * payload (bytes from the start of the stream). */
 int orc_gl_info(const uint8_t *in, size_t nbytes, uint32_t info[8]);
 
+/* ---- S4-FastPFOR in a GPU layout, GP (Section 4.4, Fig. 3) --------------- *
+ * Blocks of 128 deltas as in GL (any kind, restarting from the block's first
+ * value F); each block is bit packed at a width b' <= b and the deltas
+ * >= 2^b' are exceptions: their in-block positions (a byte each) and their
+ * b - b' high bits are stored after the low bits of each page of 32 blocks.
+ * Layout: bp_oracle.c.  Decoding unpacks, patches, then takes the prefix. */
+size_t orc_gp_bound(size_t n);
+/* The widths of one block of deltas (Section 4.4): b = orc_max_bits, b' the
+ * minimizer of 128 b' + c(b') (b - b' + 8) (largest b' on a tie), c = c(b'),
+ * the number of deltas >= 2^b'. */
+void orc_pfor_choose(const uint32_t d[128], unsigned *b, unsigned *bp, unsigned *c);
+int orc_gp_encode_kind(const uint32_t *x, size_t n, int kind, uint8_t *out,
+                       size_t cap, size_t *out_bytes);
+int orc_gp_decode(const uint8_t *in, size_t nbytes, uint32_t *out, size_t cap,
+                  size_t *n_out);
+
 /* ---- intersections (Section 6) ------------------------------------------- */
 
 /* Textbook merge ("scalar"), O(m+n).  out may alias the shorter input. */

@@ -68,16 +68,18 @@ class Oracle:
         L.orc_varint_encode.restype = _sz
         L.orc_varint_decode.argtypes = [_u8p, _sz, _sz, _u32p, C.POINTER(_sz)]
         L.orc_varint_decode.restype = C.c_int
-        for f in ("orc_pl_bound", "orc_gl_bound"):
+        L.orc_pfor_choose.argtypes = [_u32p, C.POINTER(C.c_uint), C.POINTER(C.c_uint),
+                                      C.POINTER(C.c_uint)]
+        for f in ("orc_pl_bound", "orc_gl_bound", "orc_gp_bound"):
             getattr(L, f).argtypes = [_sz]
             getattr(L, f).restype = _sz
         for f in ("orc_pl_encode", "orc_gl_encode"):
             getattr(L, f).argtypes = [_u32p, _sz, _u8p, _sz, C.POINTER(_sz)]
             getattr(L, f).restype = C.c_int
-        for f in ("orc_pl_encode_kind", "orc_gl_encode_kind"):
+        for f in ("orc_pl_encode_kind", "orc_gl_encode_kind", "orc_gp_encode_kind"):
             getattr(L, f).argtypes = [_u32p, _sz, C.c_int, _u8p, _sz, C.POINTER(_sz)]
             getattr(L, f).restype = C.c_int
-        for f in ("orc_pl_decode", "orc_gl_decode"):
+        for f in ("orc_pl_decode", "orc_gl_decode", "orc_gp_decode"):
             getattr(L, f).argtypes = [_u8p, _sz, _u32p, _sz, C.POINTER(_sz)]
             getattr(L, f).restype = C.c_int
         L.orc_stream_count.argtypes = [_u8p, _sz, C.POINTER(_sz)]
@@ -230,6 +232,21 @@ class Oracle:
 
     def gl_decode(self, data: bytes) -> np.ndarray:
         return self._decode(self.lib.orc_gl_decode, data)
+
+    def gp_encode(self, x, kind: int = 0) -> bytes:
+        """S4-FastPFOR in the GPU layout (GP)."""
+        return self._encode_kind(self.lib.orc_gp_encode_kind, self.lib.orc_gp_bound, x, kind)
+
+    def gp_decode(self, data: bytes) -> np.ndarray:
+        return self._decode(self.lib.orc_gp_decode, data)
+
+    def pfor_choose(self, d) -> tuple:
+        """(b, b', c) of one block of 128 deltas (Section 4.4)."""
+        d = _u32(d)
+        assert d.size == 128
+        b, bp, c = C.c_uint(0), C.c_uint(0), C.c_uint(0)
+        self.lib.orc_pfor_choose(d, C.byref(b), C.byref(bp), C.byref(c))
+        return int(b.value), int(bp.value), int(c.value)
 
     def gl_info(self, data: bytes) -> dict:
         buf = np.frombuffer(bytes(data), np.uint8).copy()

@@ -142,3 +142,72 @@ def gl_stream(x, kind: int = D4) -> bytes:
     out[off_bw:off_bw + nb] = bytes(widths)
     out[off_payload:] = le32(payload)
     return bytes(out)
+
+
+def pfor_widths(d):
+    """Section 4.4 by exhaustive search: b, and the b' of [0, b] with the
+    lowest 128 b' + c(b') (b - b' + 8), the largest on a tie; c(b') counts
+    the deltas that need more than b' bits."""
+    b = bits_of(max(d))
+    best = None
+    for bp in range(b + 1):
+        c = sum(1 for v in d if bits_of(v) > bp)
+        cost = 128 * bp + c * (b - bp + 8)
+        if best is None or cost <= best[0]:
+            best = (cost, bp, c)
+    return b, best[1], best[2]
+
+
+def gp_stream(x, kind: int = D4) -> bytes:
+    """GP layout (S4-FastPFOR, ours): see the oracle header for the fields."""
+    x = [int(v) for v in x]
+    n = len(x)
+    nb = (n + 127) // 128
+    npg = (nb + 31) // 32
+
+    def up16(v):
+        return (v + 15) // 16 * 16
+
+    off_first = 64
+    off_spo = off_first + up16(4 * nb)
+    off_meta = off_spo + up16(4 * (npg + 1))
+    off_payload = off_meta + up16(4 * nb)
+    first, meta, payload, spo = [], [], [], []
+    for p in range(npg):
+        spo.append(len(payload))
+        positions, highs = [], []
+        for k in range(32 * p, min(nb, 32 * p + 32)):
+            blk = x[128 * k:128 * k + 128]
+            F = blk[0]
+            full = list(blk)
+            for i in range(len(blk), 128):
+                full.append(reference(kind, full, i, F))
+            d = deltas(kind, full, F)
+            b, bp, c = pfor_widths(d)
+            first.append(F)
+            meta += [bp, b - bp, c, 0]
+            payload += gl_block_words([v % 2**bp for v in d], bp)
+            for i, v in enumerate(d):
+                if bits_of(v) > bp:
+                    positions.append(i)
+                    highs.append((v >> bp, b - bp))
+        pos_bytes = bytes(positions) + bytes(-len(positions) % 4)
+        payload += [int.from_bytes(pos_bytes[i:i + 4], "little")
+                    for i in range(0, len(pos_bytes), 4)]
+        acc, pos = 0, 0
+        for v, w in highs:
+            acc = bitstring_put(acc, pos, v, w)
+            pos += w
+        payload += [(acc >> (32 * k)) & 0xFFFFFFFF for k in range((pos + 31) // 32)]
+        payload += [0] * (-len(payload) % 4)
+    spo.append(len(payload))
+    total = off_payload + 4 * len(payload)
+    out = bytearray(total)
+    hdr = [0x34504742, 3, n, nb, npg, len(payload), off_first, off_spo, off_meta,
+           off_payload, total & 0xFFFFFFFF, total >> 32, kind, 0, 0, 0]
+    out[0:64] = le32(hdr)
+    out[off_first:off_first + 4 * nb] = le32(first)
+    out[off_spo:off_spo + 4 * (npg + 1)] = le32(spo)
+    out[off_meta:off_meta + 4 * nb] = bytes(meta)
+    out[off_payload:] = le32(payload)
+    return bytes(out)

@@ -53,6 +53,17 @@ MUTANTS = [
      "for (int s = 0; s < 4; s++) t[s] += v[s];"),
     ("gl kind not in header", "                      (uint32_t)kind,\n", "                      0u,\n"),
     ("pl decode ignores kind", "const int pkind = prefix_kind(kind);", "const int pkind = ORC_P_D4;"),
+    ("pfor cost without the position byte",
+     "const uint64_t cost = 128ull * bp + (uint64_t)c * (b - bp + 8);",
+     "const uint64_t cost = 128ull * bp + (uint64_t)c * (b - bp);"),
+    ("pfor tie to the smaller width", "    if (128ull * bp + (uint64_t)c * (b - bp + 8) == best_cost) {",
+     "    if (0) {"),
+    ("pfor exception test off by one", "      if (orc_bits(d[i]) > bp) c++;\n    const uint64_t cost",
+     "      if (orc_bits(d[i]) > bp + 1) c++;\n    const uint64_t cost"),
+    ("pfor high bits not shifted", "high[ne] = d[i] >> bp;", "high[ne] = d[i];"),
+    ("pfor patch before the low bits", "d[q] |= get_bits(payload + high_w, bit, w) << bp;",
+     "d[q] |= get_bits(payload + high_w, bit, w);"),
+    ("pfor positions not padded to a word", "    wpos += (ne + 3) / 4;", "    wpos += ne / 4;"),
 ]
 
 

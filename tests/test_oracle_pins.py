@@ -203,6 +203,76 @@ def test_variant_sizes_order(orc):
     assert sizes == sorted(sizes)
 
 
+# ---- S4-FastPFOR (Section 4.4) ------------------------------------------------
+
+def test_fig3_fastpfor_block(orc):
+    g = read_golden("fig3_fastpfor.txt")
+    d = [int(v) for v in g["prefix"]] + [i % 4 for i in range(5, 128)]
+    b, bp, c = orc.pfor_choose(d)
+    assert (b, bp, c) == (int(g["b"][0]), int(g["b_prime"][0]), int(g["exceptions"][0]))
+    assert brute.pfor_widths(d) == (b, bp, c)
+    exc = [i for i, v in enumerate(d) if v >> bp]
+    assert exc == [int(g["position"][0])]
+    assert d[exc[0]] >> bp == int(g["high"][0])
+    assert (int(g["high"][0]) << bp) | (d[exc[0]] & ((1 << bp) - 1)) == d[exc[0]]
+
+
+def test_pfor_choose_against_exhaustive_search(orc):
+    rng = np.random.default_rng(44)
+    for trial in range(300):
+        kind = trial % 3
+        if kind == 0:    # small values with a few large outliers
+            d = rng.geometric(0.3, 128).astype(np.uint64)
+            d[rng.choice(128, rng.integers(0, 12), replace=False)] = rng.integers(
+                1 << 10, 1 << 32, 1)
+        elif kind == 1:  # one width everywhere
+            d = rng.integers(0, 1 << int(rng.integers(0, 33)), 128, dtype=np.uint64)
+        else:            # ties are likely: values 0/1 and one large value
+            d = rng.integers(0, 2, 128).astype(np.uint64)
+            d[int(rng.integers(0, 128))] = 1 << int(rng.integers(1, 32))
+        d = (d & 0xFFFFFFFF).astype(np.uint32)
+        assert orc.pfor_choose(d) == brute.pfor_widths(d.tolist()), d.tolist()
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("n", [0, 1, 5, 127, 128, 129, 4096, 4097, 2 * 4096 + 15 * 128 + 3])
+def test_gp_stream_matches_bitwise_construction(orc, kind, n):
+    """GP streams byte for byte against the bit-at-a-time construction, on
+    lists with outliers (clustered runs with large jumps) so that blocks have
+    exceptions of several widths."""
+    rng = np.random.default_rng(700 + 10 * n + kind)
+    gaps = rng.geometric(0.2, n).astype(np.uint64)
+    jumps = rng.random(n) < 0.03
+    gaps[jumps] = rng.integers(1 << 8, 1 << 20, int(jumps.sum()))
+    x = np.cumsum(gaps).astype(np.uint32)
+    data = orc.gp_encode(x, kind)
+    assert data == brute.gp_stream(x, kind)
+    assert np.array_equal(orc.gp_decode(data), x)
+    if n >= 128 and kind == 0:
+        meta = np.frombuffer(data, np.uint8)
+        hdr = meta[:64].view(np.uint32)
+        c = meta[int(hdr[8]) + 2:int(hdr[8]) + 4 * int(hdr[3]):4]
+        assert c.sum() > 0  # the outliers became exceptions
+
+
+def test_gp_roundtrip_every_width(orc):
+    """Lists whose deltas reach every width 0..32, in the GP layout; patching
+    never makes a list longer than GL (b' = b is always a candidate)."""
+    rng = np.random.default_rng(45)
+    for b in range(0, 33):
+        n = 3000
+        top = (1 << 32) - 1
+        step = max(1, min(top // n, (1 << b) // 4 if b >= 2 else 1))
+        x = np.unique(np.cumsum(rng.integers(1, step + 1, n, dtype=np.uint64)) & top)
+        x = x.astype(np.uint32)
+        for kind in range(4):
+            gp = orc.gp_encode(x, kind)
+            assert np.array_equal(orc.gp_decode(gp), x)
+            gl = orc.gl_encode(x, kind)
+            # per block: 4 B of meta vs 1 B width; payload never larger
+            assert len(gp) <= len(gl) + 3 * ((x.size + 127) // 128) + 16 * (x.size // 4096 + 2)
+
+
 # ---- containers -------------------------------------------------------------
 
 EDGE_N = [0, 1, 2, 3, 4, 5, 127, 128, 129, 255, 256, 257, 2047, 2048, 2049,
