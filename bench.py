@@ -45,8 +45,9 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--lists", type=int, default=32)
-    p.add_argument("--layout", choices=["gpu", "paper"], default="gpu",
-                   help="stream layout of the timed decode (paper: the Section 4.3 layout)")
+    p.add_argument("--layout", choices=["gpu", "paper", "pfor"], default="gpu",
+                   help="stream layout of the timed decode (paper: the Section 4.3 layout; "
+                        "pfor: S4-FastPFOR-D4 in the GPU page layout)")
     p.add_argument("--log2n", type=int, default=26)
     p.add_argument("--no-extra", action="store_true", help="skip secondary measurements")
     p.add_argument("--no-e2e", action="store_true")
@@ -205,12 +206,13 @@ def load_peaks():
 # ---- the oracle as a CPU baseline --------------------------------------------------------
 
 def oracle_decode_rate(encs, ns, threads: int, layout: int = 1):
-    """Decode the given streams (GL, or PL if layout is 0) with the scalar
-    oracle on `threads` host threads; returns (Gint/s, seconds, threads)."""
+    """Decode the given streams (GL, PL if layout is 0, GP if 3) with the
+    scalar oracle on `threads` host threads; returns (Gint/s, seconds,
+    threads)."""
     from concurrent.futures import ThreadPoolExecutor
     from oracle import Oracle
     orc = Oracle()
-    dec = orc.gl_decode if layout == 1 else orc.pl_decode
+    dec = {0: orc.pl_decode, 1: orc.gl_decode, 3: orc.gp_decode}[layout]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
         outs = list(ex.map(lambda e: dec(e.tobytes()), encs))
@@ -278,11 +280,80 @@ def time_launches(stream, fn, steps: int, warmup: int):
     return e0.elapsed_time(e1) / steps
 
 
+def time_graph(stream, fn, reps: int):
+    """Capture `reps` back-to-back calls of fn() in one CUDA graph, replay it
+    (after one warm-up replay) and return ms per call from CUDA events: the
+    per-launch CPU overhead drops out, which matters for launches of a few
+    microseconds."""
+    import torch
+    with torch.cuda.stream(stream):
+        fn()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(reps):
+            fn()
+    with torch.cuda.stream(stream):
+        g.replay()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def gl_widths(enc: np.ndarray) -> np.ndarray:
     """Bit widths of the blocks of a GL stream (from its header fields)."""
     h = enc[:64].view(np.uint32)
     nb, off_bw = int(h[3]), int(h[8])
     return enc[off_bw:off_bw + nb]
+
+
+def unpack_sweep(stream, reps: int = 20, lists: int = 12, n: int = 1 << 20):
+    """Unpacking speed per bit width (Section 7.4, Fig. 4) on the GPU: for
+    b = 0..32 and each kind, `lists` GL lists of n integers whose blocks all
+    have width b (stepped walks modulo 2^32, BP_ENCODE_ANY_ORDER), decoded
+    by one bp_decode_batch (the product kernels) and by bp_decode_ablation
+    with the prefix integrated (one pass) or applied as a separate pass over
+    a block buffer in shared memory (two pass, Fig. 4a).  12 x 2^20 integers: 48 MiB out plus at most
+    48 MiB in, so repeated launches run from L2 and time the unpacking, not
+    HBM.  Gint/s, CUDA events over `reps` launches captured in one CUDA
+    graph."""
+    import torch
+    import workloads as W
+    from paper_1401_6399_gb300 import api, capi
+    GL = capi.BP_LAYOUT_GPU
+    total = lists * n
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    res = {}
+    for kname, kind in (("D4", 0), ("DM", 1), ("D2", 2), ("D1", 3)):
+        rows = {"batch": [], "one_pass": [], "two_pass": []}
+        for b in range(33):
+            xs = [W.stepped_walk(n, b, 0x7000 + 64 * b + 8 * kind + i) for i in range(lists)]
+            encs = encode_all_kind(xs, GL, kind | capi.BP_ENCODE_ANY_ORDER)
+            batch = api.ListBatch(encs, [n] * lists, GL)
+            want = torch.from_numpy(np.concatenate(xs).view(np.int32)).to("cuda")
+            for mode, fn in (("batch", lambda: batch.decode_into(out, status, stream)),
+                             ("one_pass", lambda: batch.ablation_into(out, status, 0, stream)),
+                             ("two_pass", lambda: batch.ablation_into(out, status, 1, stream))):
+                out.fill_(-1)
+                with torch.cuda.stream(stream):
+                    fn()
+                stream.synchronize()
+                assert int(status.item()) == 0 and torch.equal(out, want), (kname, b, mode)
+                ms = time_graph(stream, fn, reps)
+                rows[mode].append(round(total / (ms * 1e-3) / 1e9, 1))
+            del batch, want, encs, xs
+        gain = [round(o / t, 3) for o, t in zip(rows["one_pass"], rows["two_pass"])]
+        res[kname] = {**rows, "integration_gain": gain,
+                      "gain_range": [min(gain[1:32]), max(gain[1:32])]}
+    del out
+    torch.cuda.empty_cache()
+    return {"widths": "0..32", "ints_per_launch": total, "gints": res}
 
 
 def pair_sweep(stream, reps: int):
@@ -409,27 +480,11 @@ def pair_batch(stream, reps: int, pairs: int = 64):
     return out
 
 
-def batched_queries(stream, reps: int, plain_queries: int):
-    """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
-    2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
-    100,000 queries of 2-5 terms drawn in proportion to list length.  One
-    autotuned, CUDA-graph-captured bp_query_batch vs bp_query_one per query."""
+def graph_batch(idx, terms, toff, total, stream, reps):
+    """bp_query_batch over idx captured in a CUDA graph and replayed `reps`
+    times; returns (ms per batch, answers, offsets, counts)."""
     import torch
-    import workloads as W
-    from paper_1401_6399_gb300 import api, autotune, capi
-    t0 = time.time()
-    lens = W.zipf_lengths(1 << 19, 1_500_000_000, 1 << 24)
-    vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
-    idx = api.Index(vals, offs)
-    terms, toff = W.queries(lens, 100_000, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
-    setup_s = time.time() - t0
-    # autotune on a 5,000-query sample of the batch
-    sample_n = 5000
-    tuned = autotune.tune_queries(idx, terms[: int(toff[sample_n])], toff[: sample_n + 1],
-                                  reps=2)
-    # exact output size, then a graph-captured batch
-    _, o, _ = idx.query_batch(terms, toff, out_cap=1 << 30, on_device=True)
-    total = int(o[-1])
+    from paper_1401_6399_gb300 import capi
     nq = toff.size - 1
     dev = "cuda"
     d_terms = torch.from_numpy(terms.view(np.int32).copy()).to(dev)
@@ -458,10 +513,56 @@ def batched_queries(stream, reps: int, plain_queries: int):
             g.replay()
         e1.record(stream)
         e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    assert int(st.item()) == 0
+    assert int(st.item()) == 0, f"bp_query_batch status {int(st.item())}"
+    return e0.elapsed_time(e1) / reps, out[:total], out_off, counts
+
+
+def batched_queries(stream, reps: int, plain_queries: int):
+    """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
+    2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
+    100,000 queries of 2-5 terms drawn in proportion to list length.  One
+    autotuned, CUDA-graph-captured bp_query_batch vs bp_query_one per query."""
+    import torch
+    import workloads as W
+    from paper_1401_6399_gb300 import api, autotune, capi
+    t0 = time.time()
+    lens = W.zipf_lengths(1 << 19, 1_500_000_000, 1 << 24)
+    vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
+    idx = api.Index(vals, offs)
+    terms, toff = W.queries(lens, 100_000, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
+    setup_s = time.time() - t0
+    # autotune on a 5,000-query sample of the batch
+    sample_n = 5000
+    tuned = autotune.tune_queries(idx, terms[: int(toff[sample_n])], toff[: sample_n + 1],
+                                  reps=2)
+    # exact output size, then a graph-captured batch
+    _, o, _ = idx.query_batch(terms, toff, out_cap=1 << 30, on_device=True)
+    total = int(o[-1])
+    nq = toff.size - 1
+    dev = "cuda"
+    ms, out, out_off, counts = graph_batch(idx, terms, toff, total, stream, reps)
     o = out_off.cpu().numpy().view(np.uint64)
     c = counts.cpu().numpy().view(np.uint32)
+    # the same batch over hybrid indexes (hyb+m2): lists with average gap <= B
+    # stored as bitmaps of 2^25 bits; the answers must be the same
+    hybrid = {}
+    for B in (8, 16, 32):
+        h0 = time.time()
+        hidx = api.Index(vals, offs, hybrid_B=B, universe=1 << 25)
+        enc_s = time.time() - h0
+        hms, hout, hoff, hcnt = graph_batch(hidx, terms, toff, total, stream, reps)
+        assert torch.equal(hoff, out_off) and torch.equal(hcnt, counts)
+        assert torch.equal(hout, out), f"hybrid B={B} answers differ"
+        nbm = int((hidx.h_lists["layout"] == capi.BP_LAYOUT_BITMAP).sum())
+        hybrid[f"B{B}"] = {"bitmap_lists": nbm,
+                           "bitmap_postings": int(lens[hidx.h_lists["layout"] ==
+                                                       capi.BP_LAYOUT_BITMAP].sum()),
+                           "ms_per_batch": round(hms, 3), "queries_per_s": round(nq / (hms * 1e-3), 1),
+                           "index_bytes": hidx.compressed_bytes,
+                           "bits_per_posting": round(8 * hidx.compressed_bytes / int(lens.sum()), 3),
+                           "encode_s": round(enc_s, 1)}
+        del hidx, hout, hoff, hcnt
+        torch.cuda.empty_cache()
     # plain per-query path on the first queries (decode every list, then
     # intersect pairwise), launched back to back; same answers required
     qn = min(plain_queries, nq)
@@ -504,7 +605,7 @@ def batched_queries(stream, reps: int, plain_queries: int):
             "speedup_vs_plain": round(qps / qps_plain, 1), "answer_values": total,
             "index_postings": int(lens.sum()), "index_bytes": idx.compressed_bytes,
             "bits_per_posting": round(8 * idx.compressed_bytes / int(lens.sum()), 3),
-            "tuned": tuned["best"], "setup_s": round(setup_s, 1)}
+            "tuned": tuned["best"], "setup_s": round(setup_s, 1), "hybrid": hybrid}
 
 
 def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
@@ -562,13 +663,17 @@ def run_ours(args, rank, world, local):
     L = args.lists
     seed = SEED_BASE + 4096 * rank
     lists = make_lists("uniform", L, n, UNIVERSE, seed)
-    layout = capi.BP_LAYOUT_PAPER if args.layout == "paper" else capi.BP_LAYOUT_GPU
+    layout = {"paper": capi.BP_LAYOUT_PAPER, "gpu": capi.BP_LAYOUT_GPU,
+              "pfor": capi.BP_LAYOUT_PFOR}[args.layout]
+    lay_name = {capi.BP_LAYOUT_PAPER: "pl", capi.BP_LAYOUT_GPU: "gl",
+             capi.BP_LAYOUT_PFOR: "gp"}[layout]
     encs = encode_all(lists, layout)
     batch = api.ListBatch(encs, [n] * L, layout)
     # kernels of one bp_decode_batch call: GL the D4 kernel and the one for
     # other kinds (it leaves at once on D4 lists); PL plan, parse, resolve,
     # emit, leftover, column sums, three scan kernels, two decode kernels, tail
-    launches_per_step = 2 if layout == capi.BP_LAYOUT_GPU else 12
+    launches_per_step = {capi.BP_LAYOUT_GPU: 2, capi.BP_LAYOUT_PAPER: 12,
+                         capi.BP_LAYOUT_PFOR: 1}[layout]
     total_n = n * L
     out = torch.empty(total_n, dtype=torch.int32, device="cuda")
     status = api.status_tensor()
@@ -621,12 +726,14 @@ def run_ours(args, rank, world, local):
     traffic = profiled_traffic(sha) if layout == capi.BP_LAYOUT_GPU else None
 
     result = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC if layout != capi.BP_LAYOUT_PFOR else "S4-FastPFOR-D4 decoded Gint/s",
+        "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": f"decode {L} lists x 2^{args.log2n} uniform uint32 of [0,2^29) "
-                               f"per GPU, S4-BP128-D4 {'GPU' if layout else 'paper'} layout, "
+                               f"per GPU, "
+                               f"{ {'gl': 'S4-BP128-D4 GPU', 'pl': 'S4-BP128-D4 paper', 'gp': 'S4-FastPFOR-D4 GPU page'}[lay_name]} layout, "
                                "one bp_decode_batch call",
                    "lists_per_gpu": L, "ints_per_list": n,
                    "compressed_bytes_per_gpu": comp_bytes,
@@ -639,9 +746,10 @@ def run_ours(args, rank, world, local):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "gl_decode_kernel<false> (+ gl_decode_other_kernel, empty "
-                               "for D4 lists; both timed)" if layout else
-                               "PL decode call (all its kernels)",
+                     "kernel": {"gl": "gl_decode_kernel<false> (+ gl_decode_other_kernel, "
+                                      "empty for D4 lists; both timed)",
+                                "pl": "PL decode call (all its kernels)",
+                                "gp": "gp_decode_kernel<false>"}[lay_name],
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "frac_of_nominal_8TBs": round(achieved / 8000.0, 4)},
     }
@@ -652,7 +760,7 @@ def run_ours(args, rank, world, local):
         # decode + sum (compressed bytes only)
         sums = torch.zeros(L, dtype=torch.int64, device="cuda")
         ms_sum = time_launches(stream, lambda: batch.sum_into(sums, status, stream), reps, 2)
-        extra[f"{'gl' if layout else 'pl'}_decode_sum_uniform"] = {
+        extra[f"{lay_name}_decode_sum_uniform"] = {
             "gints": round(total_n / (ms_sum * 1e-3) / 1e9, 2), "ms": round(ms_sum, 4),
             "gbs_compressed": round(comp_bytes / (ms_sum * 1e-3) / 1e9, 1)}
         # clustered lists
@@ -667,7 +775,31 @@ def run_ours(args, rank, world, local):
             "gints": round(total_n / (ms_c * 1e-3) / 1e9, 2), "ms": round(ms_c, 4),
             "bits_per_int": round(8 * cbatch.compressed_bytes / total_n, 3),
             "hbm_gbs": round((cbatch.compressed_bytes + 4 * total_n) / (ms_c * 1e-3) / 1e9, 1)}
-        del cbatch, cl
+        del cbatch
+        # S4-FastPFOR (GP layout, Section 4.4) on the same uniform and
+        # clustered lists, D4 and D1 (the paper's query experiments use D1)
+        pfor = {}
+        for dname, data_lists in (("uniform", lists), ("clustered", cl)):
+            want = torch.from_numpy(np.concatenate(data_lists).view(np.int32)).to("cuda")
+            for kname, kind in (("D4", capi.BP_DELTA_D4), ("D1", capi.BP_DELTA_D1)):
+                gb = api.ListBatch(encode_all_kind(data_lists, capi.BP_LAYOUT_PFOR, kind),
+                                   [n] * L, capi.BP_LAYOUT_PFOR)
+                with torch.cuda.stream(stream):
+                    gb.decode_into(out, status, stream)
+                stream.synchronize()
+                assert int(status.item()) == 0 and torch.equal(out, want)
+                ms_g = time_launches(stream, lambda: gb.decode_into(out, status, stream),
+                                     max(3, reps // 5), 1)
+                gl_bytes = sum(e.size for e in encode_all_kind(data_lists, capi.BP_LAYOUT_GPU,
+                                                                kind))
+                pfor[f"{dname}_{kname}"] = {
+                    "gints": round(total_n / (ms_g * 1e-3) / 1e9, 2), "ms": round(ms_g, 4),
+                    "bits_per_int": round(8 * gb.compressed_bytes / total_n, 3),
+                    "gl_bits_per_int": round(8 * gl_bytes / total_n, 3)}
+                del gb
+            del want
+        extra["gp_decode_s4fastpfor"] = pfor
+        del cl
         # paper layout
         pbatch = api.ListBatch(encode_all(lists, capi.BP_LAYOUT_PAPER), [n] * L,
                                capi.BP_LAYOUT_PAPER)
@@ -704,6 +836,10 @@ def run_ours(args, rank, world, local):
         extra["decode_kinds_uniform"] = kinds
         del out
         torch.cuda.empty_cache()
+        try:
+            extra["unpack_sweep"] = unpack_sweep(stream)
+        except Exception as e:
+            extra["unpack_sweep"] = {"error": repr(e)[:300]}
         try:
             extra["pair_sweep"] = pair_sweep(stream, reps=20)
         except Exception as e:  # report, do not hide the headline
@@ -764,7 +900,7 @@ def run_ours(args, rank, world, local):
         val, dt, used = oracle_decode_rate(encs[:k], [n] * k, threads, layout)
         result["cpu_baseline"] = {
             "value": round(val, 4), "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{k} of the {L} {'GL' if layout else 'PL'}-encoded lists "
+            "sample": f"{k} of the {L} {lay_name.upper()}-encoded lists "
                       f"(2^{args.log2n} ints each) decoded by "
                       f"the scalar C oracle on {used} threads, {dt:.1f} s wall"}
     if rank == 0:

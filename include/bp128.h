@@ -67,7 +67,29 @@ typedef enum {
    * total bytes (u64), zeros; then first[nblocks] u32 (x[128k]),
    * sbo[nsuper+1] u32 (payload word offset of every 32nd block),
    * bw[nblocks] u8 (bit widths), payload words; sections 16-byte aligned. */
-  BP_LAYOUT_GPU = 1
+  BP_LAYOUT_GPU = 1,
+  /* A bitmap over the docID universe, for the long lists of a hybrid index
+   * (the hyb+m2 framework the paper's query experiments use: lists whose
+   * average gap is at most B are stored as bitmaps, the others compressed;
+   * Section 7.7).  Header (16 bytes, u32 little endian): magic 0x314D5042,
+   * layout 2, n, words; then `words` u32 (a multiple of 4): bit v%32 of
+   * word v/32 is set iff v is in the list.  Only bp_query_batch reads it. */
+  BP_LAYOUT_BITMAP = 2,
+  /* S4-FastPFOR (Section 4.4, Fig. 3) in a GPU layout: GL's blocks (any
+   * kind of differential coding, each restarting from its first value) and
+   * pages of 32 blocks, every block bit packed at a width b' <= b chosen to
+   * minimize 128 b' + c (b - b' + 8) (c: deltas >= 2^b', the exceptions).
+   * Header (16 u32): magic 0x34504742, 3, n, nblocks, npages, payload
+   * words, off_first, off_spo, off_meta, off_payload, total bytes (u64),
+   * kind, 0, 0, 0; then first[nblocks] u32, spo[npages+1] u32 (payload
+   * word offset of each page), meta[nblocks] 4 bytes {b', b - b', c, 0},
+   * payload; sections 16-byte aligned.  Page p: the b' low bits of each of
+   * its blocks (4 b' words, GL order), then the c position bytes of each
+   * block (ascending, zero-padded to a word), then the b - b' high bits of
+   * each exception in order (LSB first, zero-padded to a word), the page
+   * zero-padded to 4 words.  Decoded by bp_decode, bp_decode_sum and
+   * bp_decode_batch; not by the intersection calls. */
+  BP_LAYOUT_PFOR = 3
 } bp_layout;
 
 /* Kind of differential coding of a stream (Section 5), stored in its
@@ -143,7 +165,13 @@ int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
               size_t cap, size_t *out_bytes, int nthreads);
 
 /* bp_encode with the kind of differential coding `delta` (bp_delta);
- * bp_encode is this call with BP_DELTA_D4.  BP_ERR_ARG for an unknown kind. */
+ * bp_encode is this call with BP_DELTA_D4.  BP_ERR_ARG for an unknown kind.
+ * delta may be or-ed with BP_ENCODE_ANY_ORDER: the input is then any
+ * sequence of uint32 (deltas modulo 2^32; decoding returns it exactly, as
+ * the codec's arithmetic is modular) instead of a strictly increasing
+ * posting list.  Such streams are for decoding only: the intersection calls
+ * assume sorted lists. */
+#define BP_ENCODE_ANY_ORDER 0x100
 int bp_encode_kind(const uint32_t *in, size_t n, int layout, int delta,
                    uint8_t *out, size_t cap, size_t *out_bytes, int nthreads);
 
@@ -166,6 +194,16 @@ size_t bp_index_bound(const uint64_t *offs, uint32_t count);
 int bp_index_encode(const uint32_t *values, const uint64_t *offs,
                     uint32_t count, uint8_t *out, size_t cap, bp_list *lists,
                     size_t *out_bytes, int nthreads);
+
+/* Hybrid index (hyb+m2): as bp_index_encode, except that every list whose
+ * average gap is at most B (n * B >= universe) is stored as a
+ * BP_LAYOUT_BITMAP of `universe` bits (every value must be below it).
+ * B = 0 stores no bitmap.  lists[i].layout tells which form each list took. */
+size_t bp_index_hybrid_bound(const uint64_t *offs, uint32_t count, uint32_t universe,
+                             uint32_t B);
+int bp_index_encode_hybrid(const uint32_t *values, const uint64_t *offs, uint32_t count,
+                           uint32_t universe, uint32_t B, uint8_t *out, size_t cap,
+                           bp_list *lists, size_t *out_bytes, int nthreads);
 
 /* Fill lists[i].unit_base for a batch of `count` lists of one layout and
  * return the total number of work units (GL: groups of 32 blocks; PL: blocks
@@ -211,6 +249,21 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists,
                     uint32_t *d_out, uint64_t out_cap, uint64_t *d_sums,
                     void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
                     void *stream);
+
+/* Decode GPU-layout lists of any kind with the differential coding either
+ * integrated into the unpacking (two_pass = 0: each unpacked 4-vector is
+ * prefixed before it is stored, Algorithm 1) or applied as a separate pass
+ * (two_pass = 1, the regular scheme Section 7.4 measures against, Fig. 4a):
+ * each block's deltas are stored to a buffer of 128 words of shared memory
+ * per warp, read back and prefixed.  Both variants run one list-major
+ * kernel of identical structure, so the difference between them is what
+ * integration saves; the output equals bp_decode_batch's.  d_lists: device descriptors (out_offset, n,
+ * enc_offset, enc_bytes; unit_base is not used); a list that is not a GL
+ * stream records BP_ERR_CORRUPT, one that does not fit out_cap
+ * BP_ERR_CAPACITY. */
+int bp_decode_ablation(const uint8_t *d_data, const bp_list *d_lists,
+                       uint32_t count, uint32_t *d_out, uint64_t out_cap,
+                       uint32_t *d_status, int two_pass, void *stream);
 
 /* bp_decode_batch from and to host memory, for callers that keep the
  * compressed lists on the host: enqueues on `stream` the copy of h_data
@@ -282,10 +335,13 @@ int bp_intersect_pair_noalloc(const uint8_t *d_a, size_t a_bytes, size_t n_a,
 
 /* ---- conjunctive queries over a resident index -------------------------- *
  * The index is a device buffer d_data holding one GL stream per term
- * (16-byte aligned) and a device array d_lists of n_terms descriptors
- * (enc_offset, enc_bytes, n; the other fields are ignored).  A query is a
- * set of term ids; its answer is the sorted intersection of their lists
- * (Section 1 and Section 6: Set-vs-Set, from the shortest list). */
+ * (16-byte aligned) -- or, in a hybrid index, a BP_LAYOUT_BITMAP stream for
+ * the longest lists -- and a device array d_lists of n_terms descriptors
+ * (enc_offset, enc_bytes, n, layout; the other fields are ignored).  A
+ * query is a set of term ids; its answer is the sorted intersection of their
+ * lists (Section 1 and Section 6: Set-vs-Set, from the shortest list; in a
+ * hybrid index the compressed lists first, then one bit test per surviving
+ * candidate for each bitmap, as in hyb+m2). */
 
 /* Scratch needed by bp_query_batch; host copies of the index descriptors
  * and of the queries' terms, out_cap as passed to bp_query_batch. */
@@ -319,8 +375,9 @@ size_t bp_query_one_scratch_bytes(const bp_list *h_lists, uint32_t n_terms,
 /* One query, the plain way: every list of the query is decoded whole into
  * scratch, then the decoded arrays are intersected two at a time from the
  * shortest (decompress-then-intersect, Section 7.6 of the paper).  h_lists:
- * host copy of the descriptors; h_terms: k host term ids.  Answer in
- * d_out[0..count), count in *d_count (device). */
+ * host copy of the descriptors; h_terms: k host term ids (GL lists only:
+ * BP_ERR_ARG for a bitmap term).  Answer in d_out[0..count), count in
+ * *d_count (device). */
 int bp_query_one(const uint8_t *d_data, const bp_list *h_lists,
                  uint32_t n_terms, const uint32_t *h_terms, uint32_t k,
                  uint32_t *d_out, size_t out_cap, uint32_t *d_count,

@@ -108,6 +108,16 @@ class ListBatch:
                                    self.scratch.data_ptr(), self.scratch_bytes,
                                    status.data_ptr(), _stream(stream)), "bp_decode_batch")
 
+    def ablation_into(self, out: torch.Tensor, status: torch.Tensor, mode: int,
+                      stream=None) -> None:
+        """GL only: the list-major decoder with the prefix integrated (mode
+        0) or as a separate pass through shared memory (1)
+        (bp_decode_ablation)."""
+        check(capi.bp_decode_ablation(self.data.data_ptr(), self.d_lists.data_ptr(), self.count,
+                                      out.data_ptr(), out.numel(), status.data_ptr(), int(mode),
+                                      _stream(stream)),
+              "bp_decode_ablation")
+
     def decode(self) -> torch.Tensor:
         out = torch.empty(max(self.total_n, 1), dtype=torch.int32, device=self.data.device)
         st = status_tensor(self.data.device)
@@ -149,8 +159,14 @@ class Index:
     """A resident index: one GL stream per term in one device buffer, the
     descriptors on host and device, and the query calls over it."""
 
-    def __init__(self, values: np.ndarray, offs: np.ndarray, device="cuda", nthreads: int = 16):
-        host, lists = capi.bp_index_encode(values, offs, nthreads)
+    def __init__(self, values: np.ndarray, offs: np.ndarray, device="cuda", nthreads: int = 16,
+                 hybrid_B: int = 0, universe: int = 0):
+        """hybrid_B > 0: lists whose average gap is at most hybrid_B are stored
+        as bitmaps of `universe` bits (hyb+m2)."""
+        if hybrid_B:
+            host, lists = capi.bp_index_encode_hybrid(values, offs, universe, hybrid_B, nthreads)
+        else:
+            host, lists = capi.bp_index_encode(values, offs, nthreads)
         self.h_lists = lists
         self.n_terms = lists.size
         self.host_data = host

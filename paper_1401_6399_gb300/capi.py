@@ -65,11 +65,15 @@ _decl("bp_stream_kind", _int, _vp, _sz, C.POINTER(_int))
 _decl("bp_plan_lists", _u64, _vp, _u32)
 _decl("bp_index_bound", _sz, _vp, _u32)
 _decl("bp_index_encode", _int, _vp, _vp, _u32, _vp, _sz, _vp, C.POINTER(_sz), _int)
+_decl("bp_index_hybrid_bound", _sz, _vp, _u32, _u32, _u32)
+_decl("bp_index_encode_hybrid", _int, _vp, _vp, _u32, _u32, _u32, _vp, _sz, _vp, C.POINTER(_sz),
+      _int)
 _decl("bp_decode_scratch_bytes", _sz, _sz, _int)
 _decl("bp_decode", _int, _vp, _sz, _int, _sz, _vp, _sz, _vp, _sz, _vp, _vp)
 _decl("bp_decode_sum", _int, _vp, _sz, _int, _sz, _vp, _vp, _sz, _vp, _vp)
 _decl("bp_decode_batch_scratch_bytes", _sz, _vp, _u32)
 _decl("bp_decode_batch", _int, _vp, _vp, _u32, _u64, _int, _vp, _u64, _vp, _vp, _sz, _vp, _vp)
+_decl("bp_decode_ablation", _int, _vp, _vp, _u32, _vp, _u64, _vp, _int, _vp)
 _decl("bp_decode_batch_host", _int, _vp, _sz, _vp, _u32, _u64, _int, _vp, _vp, _vp, _u64, _vp,
       _vp, _sz, _vp, _vp, _vp)
 _decl("bp_query_batch_scratch_bytes", _sz, _vp, _u32, _vp, _vp, _u32, _u64)
@@ -120,8 +124,12 @@ def bp_encode_bound(n: int, layout: int) -> int:
 BP_DELTA_D4, BP_DELTA_DM, BP_DELTA_D2, BP_DELTA_D1 = 0, 1, 2, 3
 
 
+BP_ENCODE_ANY_ORDER = 0x100
+
+
 def bp_encode(x, layout: int, nthreads: int = 1, delta: int = BP_DELTA_D4) -> np.ndarray:
-    """Encode a sorted distinct uint32 array; returns the stream as uint8."""
+    """Encode a sorted distinct uint32 array (any uint32 array if delta has
+    BP_ENCODE_ANY_ORDER set); returns the stream as uint8."""
     x = np.ascontiguousarray(x, np.uint32)
     cap = bp_encode_bound(x.size, layout)
     out = np.empty(max(cap, 16), np.uint8)
@@ -171,6 +179,28 @@ def bp_index_encode(values: np.ndarray, offs: np.ndarray, nthreads: int = 8):
     return out[: max(used.value, 16)], lists
 
 
+BP_LAYOUT_BITMAP = 2
+BP_LAYOUT_PFOR = 3
+
+
+def bp_index_encode_hybrid(values: np.ndarray, offs: np.ndarray, universe: int, B: int,
+                           nthreads: int = 8):
+    """Hybrid (hyb+m2) index: lists with average gap <= B become bitmaps of
+    `universe` bits, the others GL streams; returns (uint8 buffer, BP_LIST array)."""
+    values = np.ascontiguousarray(values, np.uint32)
+    offs = np.ascontiguousarray(offs, np.uint64)
+    count = offs.size - 1
+    cap = int(lib.bp_index_hybrid_bound(offs.ctypes.data, count, universe, B))
+    out = np.empty(max(cap, 16), np.uint8)
+    lists = np.zeros(count, BP_LIST)
+    used = _sz(0)
+    check(lib.bp_index_encode_hybrid(values.ctypes.data if values.size else None,
+                                     offs.ctypes.data, count, universe, B, out.ctypes.data, cap,
+                                     lists.ctypes.data, C.byref(used), nthreads),
+          "bp_index_encode_hybrid")
+    return out[: max(used.value, 16)], lists
+
+
 # ---- device (raw pointers) ---------------------------------------------------------
 
 def bp_decode_scratch_bytes(n: int, layout: int) -> int:
@@ -198,6 +228,11 @@ def bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap,
                     d_scratch, scratch_bytes, d_status, stream) -> int:
     return lib.bp_decode_batch(d_data, d_lists, count, total_units, layout, d_out, out_cap,
                                d_sums, d_scratch, scratch_bytes, d_status, stream)
+
+
+def bp_decode_ablation(d_data, d_lists, count, d_out, out_cap, d_status, two_pass, stream) -> int:
+    return lib.bp_decode_ablation(d_data, d_lists, count, d_out, out_cap, d_status, two_pass,
+                                  stream)
 
 
 def bp_get_tuning() -> dict:

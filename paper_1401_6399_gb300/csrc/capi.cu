@@ -34,7 +34,8 @@ int decode_common(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, 
                   size_t out_cap, uint64_t *d_sum, void *d_scratch, size_t scratch_bytes,
                   uint32_t *d_status, void *stream) {
   if (!d_enc || !d_status || !aligned16(d_enc)) return BP_ERR_ARG;
-  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU && layout != BP_LAYOUT_PFOR)
+    return BP_ERR_ARG;
   if (n > bp_fmt::kMaxList) return BP_ERR_ARG;
   if (!d_sum) {
     if (!d_out && n) return BP_ERR_ARG;
@@ -45,6 +46,8 @@ int decode_common(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, 
   const uint64_t units = bp_fmt::units_of(n, layout);
   if (layout == BP_LAYOUT_GPU)
     return bp::launch_gl_decode(d_enc, src, units, d_out, n, d_sum, d_status, s);
+  if (layout == BP_LAYOUT_PFOR)
+    return bp::launch_gp_decode(d_enc, src, units, d_out, n, d_sum, d_status, s);
   return bp::launch_pl_decode(d_enc, src, units, d_out, n, d_sum, d_scratch, scratch_bytes,
                               d_status, s);
 }
@@ -211,7 +214,8 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists, uint32_t coun
                     uint64_t *d_sums, void *d_scratch, size_t scratch_bytes, uint32_t *d_status,
                     void *stream) {
   if (!d_data || !d_lists || !d_status || count == 0 || !aligned16(d_data)) return BP_ERR_ARG;
-  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU && layout != BP_LAYOUT_PFOR)
+    return BP_ERR_ARG;
   if (!d_sums && !d_out) return BP_ERR_ARG;
   ListSrc src;
   src.lists = d_lists;
@@ -220,8 +224,20 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists, uint32_t coun
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (layout == BP_LAYOUT_GPU)
     return bp::launch_gl_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_status, s);
+  if (layout == BP_LAYOUT_PFOR)
+    return bp::launch_gp_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_status, s);
   return bp::launch_pl_decode(d_data, src, total_units, d_out, out_cap, d_sums, d_scratch,
                               scratch_bytes, d_status, s);
+}
+
+int bp_decode_ablation(const uint8_t *d_data, const bp_list *d_lists, uint32_t count,
+                       uint32_t *d_out, uint64_t out_cap, uint32_t *d_status, int two_pass,
+                       void *stream) {
+  if (!d_data || !d_lists || !d_out || !d_status || count == 0 || !aligned16(d_data))
+    return BP_ERR_ARG;
+  if (two_pass != 0 && two_pass != 1) return BP_ERR_ARG;
+  return bp::launch_gl_ablation(d_data, d_lists, count, d_out, out_cap, d_status, two_pass,
+                                static_cast<cudaStream_t>(stream));
 }
 
 int bp_decode_batch_host(const uint8_t *h_data, size_t data_bytes, const bp_list *h_lists,

@@ -45,6 +45,18 @@ inline ListSrc single_list(size_t enc_bytes, size_t n, int layout) {
 int device_sm_count();
 
 // GL layout.  sums == nullptr: store into out; else sums[i] += sum of list i.
+// GP (S4-FastPFOR) lists: one warp per page of 32 blocks, unpack, patch,
+// prefix (decode_pfor.cu).
+int launch_gp_decode(const uint8_t *data, const ListSrc &src, uint64_t total_units,
+                     uint32_t *out, uint64_t out_cap, uint64_t *sums, uint32_t *status,
+                     cudaStream_t s);
+
+// bp_decode_ablation: GL lists decoded by one list-major kernel with the
+// prefix integrated (mode 0) or as a separate pass over a block buffer in
+// shared memory (1).
+int launch_gl_ablation(const uint8_t *data, const bp_list *lists, uint32_t count, uint32_t *out,
+                       uint64_t out_cap, uint32_t *status, int mode, cudaStream_t s);
+
 int launch_gl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_units,
                      uint32_t *out, uint64_t out_cap, uint64_t *sums, uint32_t *status,
                      cudaStream_t s);
@@ -72,7 +84,7 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
                        cudaStream_t s);
 // Work items of a query whose shortest list has nmin integers, and the
 // scratch of a batch from its totals (incremental forms of the above).
-uint64_t query_items(uint64_t nmin);
+uint64_t query_items_of(const bp_list &driver);  // driver: first list in Set-vs-Set order
 size_t query_batch_scratch_for(uint64_t total_terms, uint32_t nq, uint64_t out_cap,
                                uint64_t items);
 size_t query_one_scratch_bytes(const bp_list *h_lists, const uint32_t *h_terms, uint32_t k);

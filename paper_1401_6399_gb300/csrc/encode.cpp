@@ -221,6 +221,137 @@ size_t gl_size(const uint32_t *x, size_t n) {
   return g.off_payload + 4 * (size_t)w;
 }
 
+// ---- S4-FastPFOR, GPU layout (GP) ------------------------------------------
+
+struct PforBlock {
+  uint8_t bp, w, c;  // low width b', high width b - b', exceptions
+};
+
+// Section 4.4: b' in [0, b] minimizing 128 b' + c(b') (b - b' + 8), the
+// largest on a tie; c(b') from a histogram of the deltas' widths.
+PforBlock pfor_choose(const uint32_t *d) {
+  unsigned hist[33] = {0};
+  for (unsigned i = 0; i < 128; i++) hist[width_of(d[i])]++;
+  unsigned b = 32;
+  while (b > 0 && hist[b] == 0) b--;
+  unsigned above = 0;  // deltas wider than the candidate b'
+  uint64_t best_cost = ~0ull;
+  PforBlock best{0, 0, 0};
+  for (int bp = (int)b; bp >= 0; bp--) {
+    const uint64_t cost = 128ull * (unsigned)bp + (uint64_t)above * (b - (unsigned)bp + 8);
+    if (cost < best_cost) {  // strictly lower: a tie keeps the larger b'
+      best_cost = cost;
+      best = PforBlock{(uint8_t)bp, (uint8_t)(b - (unsigned)bp), (uint8_t)above};
+    }
+    above += hist[bp];
+  }
+  if (best.c == 0) best.w = 0;
+  return best;
+}
+
+// Words of a page: the low bits, the position bytes and the high bits of its
+// blocks, the last two padded to a word, the page to 4 words.
+uint64_t gp_page_words(const std::vector<PforBlock> &m, size_t k0, size_t k1) {
+  uint64_t low = 0, ne = 0, hbits = 0;
+  for (size_t k = k0; k < k1; k++) {
+    low += 4ull * m[k].bp;
+    ne += m[k].c;
+    hbits += (uint64_t)m[k].c * m[k].w;
+  }
+  return (low + (ne + 3) / 4 + (hbits + 31) / 32 + 3) & ~3ull;
+}
+
+// OR v (w bits) into the little-endian bit string at `words`, bit `bit`.
+void put_field(uint8_t *words, uint64_t bit, uint32_t v, unsigned w) {
+  uint8_t *p = words + 4 * (bit >> 5);
+  const unsigned o = (unsigned)(bit & 31);
+  uint32_t cur;
+  std::memcpy(&cur, p, 4);
+  cur |= v << o;
+  std::memcpy(p, &cur, 4);
+  if (o + w > 32) {
+    std::memcpy(&cur, p + 4, 4);
+    cur |= v >> (32 - o);
+    std::memcpy(p + 4, &cur, 4);
+  }
+}
+
+int encode_pfor(const uint32_t *x, size_t n, int kind, uint8_t *out, size_t cap,
+                size_t *out_bytes, int nthreads) {
+  const bp_fmt::GpGeometry g = bp_fmt::gp_geometry(n);
+  std::vector<PforBlock> meta(g.nblocks);
+  parallel_ranges(g.nblocks, nthreads, [&](size_t lo, size_t hi) {
+    uint32_t d[128];
+    for (size_t k = lo; k < hi; k++) {
+      gl_deltas(x, n, k, kind, d);
+      meta[k] = pfor_choose(d);
+    }
+  });
+  std::vector<uint64_t> poff(g.npages + 1);
+  uint64_t w = 0;
+  for (size_t p = 0; p < g.npages; p++) {
+    poff[p] = w;
+    w += gp_page_words(meta, 32 * p, std::min(g.nblocks, 32 * p + 32));
+  }
+  poff[g.npages] = w;
+  if (w > 0xFFFFFFFFull) return BP_ERR_ARG;
+  const size_t total = g.off_payload + 4 * (size_t)w;
+  if (total > cap) return BP_ERR_CAPACITY;
+
+  std::memset(out, 0, total);
+  const uint32_t hdr[16] = {bp_fmt::kGpMagic, 3u, (uint32_t)n, (uint32_t)g.nblocks,
+                            (uint32_t)g.npages, (uint32_t)w, (uint32_t)g.off_first,
+                            (uint32_t)g.off_spo, (uint32_t)g.off_meta,
+                            (uint32_t)g.off_payload, (uint32_t)(total & 0xFFFFFFFFu),
+                            (uint32_t)((uint64_t)total >> 32), (uint32_t)kind, 0, 0, 0};
+  std::memcpy(out, hdr, 64);
+  for (size_t p = 0; p <= g.npages; p++) put_le32(out + g.off_spo + 4 * p, (uint32_t)poff[p]);
+  for (size_t k = 0; k < g.nblocks; k++) {
+    out[g.off_meta + 4 * k + 0] = meta[k].bp;
+    out[g.off_meta + 4 * k + 1] = meta[k].w;
+    out[g.off_meta + 4 * k + 2] = meta[k].c;
+  }
+  parallel_ranges(g.npages, nthreads, [&](size_t lo, size_t hi) {
+    uint32_t d[128], lowd[128], wb[128];
+    std::vector<uint8_t> pos;
+    std::vector<uint32_t> high, hw;
+    for (size_t p = lo; p < hi; p++) {
+      const size_t k0 = 32 * p, k1 = std::min(g.nblocks, k0 + 32);
+      uint8_t *page = out + g.off_payload + 4 * poff[p];
+      uint64_t wl = 0;
+      pos.clear();
+      high.clear();
+      hw.clear();
+      for (size_t k = k0; k < k1; k++) {
+        put_le32(out + g.off_first + 4 * k, x[128 * k]);
+        gl_deltas(x, n, k, kind, d);
+        const PforBlock m = meta[k];
+        const uint32_t mask = m.bp >= 32 ? 0xFFFFFFFFu : (1u << m.bp) - 1u;
+        for (unsigned i = 0; i < 128; i++) {
+          lowd[i] = d[i] & mask;
+          if (d[i] & ~mask) {  // an exception (only when b' < b)
+            pos.push_back((uint8_t)i);
+            high.push_back(d[i] >> m.bp);
+            hw.push_back(m.w);
+          }
+        }
+        pack_gl(lowd, m.bp, wb);
+        std::memcpy(page + 4 * wl, wb, 16 * (size_t)m.bp);
+        wl += 4ull * m.bp;
+      }
+      if (!pos.empty()) std::memcpy(page + 4 * wl, pos.data(), pos.size());
+      uint8_t *hbase = page + 4 * (wl + (pos.size() + 3) / 4);
+      uint64_t bit = 0;
+      for (size_t e = 0; e < high.size(); e++) {
+        put_field(hbase, bit, high[e], hw[e]);
+        bit += hw[e];
+      }
+    }
+  });
+  *out_bytes = total;
+  return BP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -274,12 +405,92 @@ int bp_index_encode(const uint32_t *values, const uint64_t *offs, uint32_t count
   return BP_OK;
 }
 
+size_t bp_index_hybrid_bound(const uint64_t *offs, uint32_t count, uint32_t universe,
+                             uint32_t B) {
+  if (!offs) return 0;
+  const size_t bm = bp_fmt::kBitmapHeader + 4 * bp_fmt::bitmap_words(universe);
+  size_t total = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    const uint64_t n = offs[i + 1] - offs[i];
+    total += (B && n * B >= universe) ? bm
+                                      : bp_fmt::up16(bp_encode_bound(n, BP_LAYOUT_GPU));
+  }
+  return total;
+}
+
+int bp_index_encode_hybrid(const uint32_t *values, const uint64_t *offs, uint32_t count,
+                           uint32_t universe, uint32_t B, uint8_t *out, size_t cap,
+                           bp_list *lists, size_t *out_bytes, int nthreads) {
+  if (!values || !offs || !out || !lists || !out_bytes || universe == 0) return BP_ERR_ARG;
+  const uint64_t words = bp_fmt::bitmap_words(universe);
+  const size_t bm_bytes = bp_fmt::kBitmapHeader + 4 * words;
+  std::vector<size_t> sizes(count);
+  std::vector<uint8_t> is_bm(count, 0);
+  std::vector<int> bad(count, 0);
+  parallel_ranges(count, nthreads, [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; i++) {
+      const uint32_t *x = values + offs[i];
+      const size_t n = offs[i + 1] - offs[i];
+      if (n > bp_fmt::kMaxList) bad[i] = BP_ERR_ARG;
+      for (size_t j = 1; j < n && !bad[i]; j++)
+        if (x[j] <= x[j - 1]) bad[i] = BP_ERR_UNSORTED;
+      if (bad[i]) continue;
+      if (B && (uint64_t)n * B >= universe) {
+        if (n && x[n - 1] >= universe) bad[i] = BP_ERR_ARG;
+        is_bm[i] = 1;
+        sizes[i] = bm_bytes;
+      } else {
+        sizes[i] = gl_size(x, n);
+      }
+    }
+  });
+  size_t pos = 0;
+  for (uint32_t i = 0; i < count; i++) {
+    if (bad[i]) return bad[i];
+    lists[i] = bp_list{pos, sizes[i], offs[i], 0, (uint32_t)(offs[i + 1] - offs[i]),
+                       is_bm[i] ? (uint32_t)BP_LAYOUT_BITMAP : (uint32_t)BP_LAYOUT_GPU, 0};
+    pos += bp_fmt::up16(sizes[i]);
+  }
+  if (pos > cap) return BP_ERR_CAPACITY;
+  std::vector<int> rc(count, BP_OK);
+  parallel_ranges(count, nthreads, [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; i++) {
+      const size_t n = offs[i + 1] - offs[i];
+      uint8_t *o = out + lists[i].enc_offset;
+      if (is_bm[i]) {
+        std::memset(o, 0, bm_bytes);
+        put_le32(o + 0, bp_fmt::kBitmapMagic);
+        put_le32(o + 4, (uint32_t)BP_LAYOUT_BITMAP);
+        put_le32(o + 8, (uint32_t)n);
+        put_le32(o + 12, (uint32_t)words);
+        uint8_t *bits = o + bp_fmt::kBitmapHeader;
+        for (size_t j = 0; j < n; j++) {
+          const uint32_t v = values[offs[i] + j];
+          bits[v >> 3] |= (uint8_t)(1u << (v & 7));  // little endian: bit v%32 of word v/32
+        }
+      } else {
+        size_t got = 0;
+        rc[i] = encode_gpu(values + offs[i], n, BP_DELTA_D4, o, bp_encode_bound(n, BP_LAYOUT_GPU),
+                           &got, 1);
+        if (rc[i] == BP_OK && got != sizes[i]) rc[i] = BP_ERR_ARG;
+      }
+      const size_t pad = bp_fmt::up16(sizes[i]) - sizes[i];
+      if (pad) std::memset(o + sizes[i], 0, pad);
+    }
+  });
+  for (uint32_t i = 0; i < count; i++)
+    if (rc[i] != BP_OK) return rc[i];
+  *out_bytes = pos;
+  return BP_OK;
+}
+
 size_t bp_encode_bound(size_t n, int layout) {
   if (layout == BP_LAYOUT_PAPER) return bp_fmt::pl_bound(n);
   if (layout == BP_LAYOUT_GPU) {
     const bp_fmt::GlGeometry g = bp_fmt::gl_geometry(n);
     return g.off_payload + 512 * g.nblocks;
   }
+  if (layout == BP_LAYOUT_PFOR) return bp_fmt::gp_bound(n);
   return 0;
 }
 
@@ -291,12 +502,16 @@ int bp_encode(const uint32_t *in, size_t n, int layout, uint8_t *out,
 int bp_encode_kind(const uint32_t *in, size_t n, int layout, int delta, uint8_t *out,
                    size_t cap, size_t *out_bytes, int nthreads) {
   if (!out || !out_bytes || (n && !in)) return BP_ERR_ARG;
-  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
+  if (layout != BP_LAYOUT_PAPER && layout != BP_LAYOUT_GPU && layout != BP_LAYOUT_PFOR)
+    return BP_ERR_ARG;
+  const bool any_order = (delta & BP_ENCODE_ANY_ORDER) != 0;
+  delta &= ~BP_ENCODE_ANY_ORDER;
   if (delta < BP_DELTA_D4 || delta > BP_DELTA_D1) return BP_ERR_ARG;
   if (n > bp_fmt::kMaxList) return BP_ERR_ARG;
-  for (size_t i = 1; i < n; i++)
+  for (size_t i = 1; i < n && !any_order; i++)
     if (in[i] <= in[i - 1]) return BP_ERR_UNSORTED;
   if (cap < bp_encode_bound(n, layout)) return BP_ERR_CAPACITY;
+  if (layout == BP_LAYOUT_PFOR) return encode_pfor(in, n, delta, out, cap, out_bytes, nthreads);
   return layout == BP_LAYOUT_PAPER ? encode_paper(in, n, delta, out, cap, out_bytes, nthreads)
                                    : encode_gpu(in, n, delta, out, cap, out_bytes, nthreads);
 }
@@ -323,6 +538,17 @@ int bp_stream_info(const uint8_t *enc, size_t enc_bytes, uint32_t *n_out,
     if (h[12] > (uint32_t)BP_DELTA_D1) return BP_ERR_CORRUPT;
     *n_out = h[2];
     *layout_out = BP_LAYOUT_GPU;
+    return BP_OK;
+  }
+  if (h[0] == bp_fmt::kGpMagic && h[1] == 3u) {
+    const bp_fmt::GpGeometry g = bp_fmt::gp_geometry(h[2]);
+    const uint64_t total = (uint64_t)h[10] | ((uint64_t)h[11] << 32);
+    if (h[3] != g.nblocks || h[4] != g.npages || h[6] != g.off_first || h[7] != g.off_spo ||
+        h[8] != g.off_meta || h[9] != g.off_payload || total != g.off_payload + 4ull * h[5] ||
+        total > enc_bytes || h[12] > (uint32_t)BP_DELTA_D1)
+      return BP_ERR_CORRUPT;
+    *n_out = h[2];
+    *layout_out = BP_LAYOUT_PFOR;
     return BP_OK;
   }
   return BP_ERR_CORRUPT;

@@ -41,7 +41,7 @@ inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 struct QScratch {
   uint32_t *sorted;    // [total_terms] term ids in SvS order
   uint32_t *base;      // [nq + 1] items per query, scanned in place
-  unsigned long long *counters;  // [0] next item, [1] arena top
+  unsigned long long *counters;  // [0] next item, [1] arena top, [2] any bitmap term
   uint32_t *item_q;    // [max_items]
   uint64_t *item_off;  // [max_items] arena offset
   uint32_t *item_cnt;  // [max_items]
@@ -94,6 +94,26 @@ QScratch q_carve(void *p, const QLayout &L) {
 
 // ---- 1. planning ---------------------------------------------------------------------
 
+// Set-vs-Set order of a query's terms: compressed lists by length, then the
+// bitmaps of a hybrid index (hyb+m2: the compressed lists are intersected
+// first and the survivors tested against the bitmaps).
+__host__ __device__ inline uint64_t svs_key(const bp_list &L) {
+  return ((uint64_t)(L.layout == BP_LAYOUT_BITMAP) << 32) | L.n;
+}
+
+// Words of the bitmaps that one work item ANDs (32 per lane).
+constexpr uint32_t kBitmapItemWords = 1024;
+
+// Work items of a query driven by list L: `chunk` blocks of a GL list each,
+// or kBitmapItemWords words (32,768 docIDs) of a bitmap.
+__host__ __device__ inline uint64_t driver_items(const bp_list &L, uint32_t chunk) {
+  if (L.layout == BP_LAYOUT_BITMAP) {
+    const uint64_t words = L.enc_bytes >= 16 ? (L.enc_bytes - 16) / 4 : 0;
+    return (words + kBitmapItemWords - 1) / kBitmapItemWords;
+  }
+  return ((L.n + 127ull) / 128 + chunk - 1) / chunk;
+}
+
 __global__ void q_plan_kernel(const bp_list *__restrict__ lists, uint32_t n_terms,
                               const uint32_t *__restrict__ terms, const uint64_t *__restrict__ toff,
                               uint32_t nq, QScratch sc, uint32_t chunk, uint32_t *status) {
@@ -102,6 +122,7 @@ __global__ void q_plan_kernel(const bp_list *__restrict__ lists, uint32_t n_term
   const uint64_t b = toff[q], e = toff[q + 1];
   const uint32_t k = (uint32_t)(e - b);
   uint32_t items = 0;
+  bool any_bitmap = false;
   if (e < b || k > (uint32_t)kMaxTerms) {
     set_status(status, BP_ERR_ARG);
   } else if (k > 0) {
@@ -112,11 +133,12 @@ __global__ void q_plan_kernel(const bp_list *__restrict__ lists, uint32_t n_term
         ok = false;
         break;
       }
-      const uint32_t nt = lists[t].n;
+      const uint64_t nt = svs_key(lists[t]);
+      if (nt >> 32) any_bitmap = true;
       uint32_t p = i;
       while (p > 0) {
         const uint32_t u = sc.sorted[b + p - 1];
-        const uint32_t nu = lists[u].n;
+        const uint64_t nu = svs_key(lists[u]);
         if (nu < nt || (nu == nt && u <= t)) break;
         sc.sorted[b + p] = u;
         p--;
@@ -126,68 +148,187 @@ __global__ void q_plan_kernel(const bp_list *__restrict__ lists, uint32_t n_term
     if (!ok) {
       set_status(status, BP_ERR_ARG);
     } else {
-      const uint32_t nb1 = (lists[sc.sorted[b]].n + 127u) / 128u;
-      items = (nb1 + chunk - 1) / chunk;
+      items = (uint32_t)driver_items(lists[sc.sorted[b]], chunk);
     }
   }
   sc.base[q] = items;
+  if (any_bitmap && sc.counters[2] == 0ull) sc.counters[2] = 1ull;
 }
 
-// Exclusive scan of a[0..n) in place by one CTA of 1024 threads; a[n] = total.
+// Exclusive scan of a[0..n) in place by one CTA of 1024 threads; a[n] =
+// total, saturated at 2^32 - 1 (more work items than any scratch holds: the
+// kernels that read a[n] then stop with BP_ERR_SCRATCH).
 __global__ void __launch_bounds__(1024) scan_u32_kernel(uint32_t *a, uint32_t n) {
-  __shared__ uint32_t s_w[32];
-  __shared__ uint32_t s_carry;
+  __shared__ uint64_t s_w[32];
+  __shared__ uint64_t s_carry;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (uint32_t base = 0; base < n; base += 1024) {
     const uint32_t i = base + threadIdx.x;
     const uint32_t x = i < n ? a[i] : 0u;
-    uint32_t incl = x;
+    uint64_t incl = x;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t t = __shfl_up_sync(kFull, incl, d);
+      const uint64_t t = __shfl_up_sync(kFull, incl, d);
       if (lane >= d) incl += t;
     }
     if (lane == 31) s_w[w] = incl;
     __syncthreads();
     if (w == 0) {
-      uint32_t v = s_w[lane], vi = v;
+      uint64_t v = s_w[lane], vi = v;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, vi, d);
+        const uint64_t t = __shfl_up_sync(kFull, vi, d);
         if (lane >= d) vi += t;
       }
       s_w[lane] = vi - v;
     }
     __syncthreads();
-    const uint32_t carry = s_carry;
-    if (i < n) a[i] = carry + s_w[w] + incl - x;
+    const uint64_t carry = s_carry;
+    if (i < n) a[i] = (uint32_t)(carry + s_w[w] + incl - x);
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = carry + s_w[w] + incl;
     __syncthreads();
   }
-  if (threadIdx.x == 0) a[n] = s_carry;
+  if (threadIdx.x == 0) a[n] = s_carry > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)s_carry;
 }
 
 // ---- 3. the persistent fused kernel --------------------------------------------------------
 
+// A term's list as the kernel sees it: a GL stream, or a bitmap (then
+// gl.payload holds its words and gl.pw their count; no other field is set).
+struct TermView {
+  bool bitmap;
+  GlView gl;
+};
+
 // 0, or the status of a term whose list cannot be used: BP_ERR_CORRUPT, or
-// BP_ERR_ARG for a list that is not D4 (the probes need D4 columns).
+// BP_ERR_ARG for a GL list that is not D4 (the probes need D4 columns).
+template <bool HYB>
 __device__ __forceinline__ uint32_t term_view(const uint8_t *data, const bp_list *lists,
-                                              uint32_t t, GlView &v) {
+                                              uint32_t t, TermView &v) {
   const bp_list L = lists[t];
-  if (!gl_view(data + L.enc_offset, L.enc_bytes, v) || v.n != L.n) return BP_ERR_CORRUPT;
-  return v.kind == 0u ? 0u : (uint32_t)BP_ERR_ARG;
+  v.bitmap = HYB && L.layout == BP_LAYOUT_BITMAP;
+  if (v.bitmap) {
+    const uint8_t *enc = data + L.enc_offset;
+    if (L.enc_bytes < 16 || (L.enc_offset & 15u)) return BP_ERR_CORRUPT;
+    const uint4 h = __ldg(reinterpret_cast<const uint4 *>(enc));
+    if (h.x != bp_fmt::kBitmapMagic || h.y != (uint32_t)BP_LAYOUT_BITMAP || h.z != L.n ||
+        16ull + 4ull * h.w > L.enc_bytes)
+      return BP_ERR_CORRUPT;
+    v.gl.payload = reinterpret_cast<const uint32_t *>(enc + 16);
+    v.gl.pw = h.w;
+    return 0u;
+  }
+  if (!gl_view(data + L.enc_offset, L.enc_bytes, v.gl) || v.gl.n != L.n) return BP_ERR_CORRUPT;
+  return v.gl.kind == 0u ? 0u : (uint32_t)BP_ERR_ARG;
+}
+
+// Clears the bits of `alive` whose candidates (value 128g + 32j + lane of
+// s_r for bit 4g+j) are not set in the bitmap: one load per candidate.
+__device__ __noinline__ uint32_t bitmap_filter(const uint32_t *__restrict__ bm, uint32_t words,
+                                               const uint32_t *s_r, uint32_t ng, uint32_t alive,
+                                               int lane) {
+  for (uint32_t g = 0; g < ng; g++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const uint32_t bit = 1u << (4 * g + j);
+      const uint32_t x = s_r[128u * g + 32 * j + lane];
+      if ((alive & bit) && !((x >> 5) < words && ((__ldg(bm + (x >> 5)) >> (x & 31u)) & 1u)))
+        alive &= ~bit;
+    }
+  return alive;
+}
+
+// One work item of a query whose terms are all bitmaps.  Not inlined: it
+// keeps its registers out of the Set-vs-Set loop of q_main_kernel.
+__device__ __noinline__ void bitmap_and_item(const uint8_t *__restrict__ data,
+                                             const bp_list *__restrict__ lists, const TermView &V1,
+                                             const uint32_t *sorted, uint32_t k, uint32_t c,
+                                             uint32_t q, uint32_t item, QScratch sc,
+                                             uint64_t arena_cap, uint32_t *s_r, int lane,
+                                             uint32_t *status) {
+  // Bitmaps sort last, so every term is a bitmap: AND kBitmapItemWords
+  // words of all of them (lane l keeps words 32i + l in s_r), then write
+  // the set bits of the result straight to the arena
+  const uint32_t w0 = kBitmapItemWords * c;
+  uint32_t any = 0;
+#pragma unroll 8
+  for (uint32_t i = 0; i < 32; i++) {
+    const uint32_t wi = w0 + 32u * i + lane;
+    const uint32_t x = wi < V1.gl.pw ? __ldg(V1.gl.payload + wi) : 0u;
+    s_r[32u * i + lane] = x;
+    any |= x;
+  }
+  for (uint32_t t = 1; t < k && __any_sync(kFull, any != 0u); t++) {
+    TermView F;
+    uint32_t tf = term_view<true>(data, lists, sorted[t], F);
+    if (tf == 0u && !F.bitmap) tf = BP_ERR_CORRUPT;  // cannot follow a bitmap
+    if (tf != 0u) {
+      if (lane == 0) set_status(status, tf);
+      any = 0;
+      break;
+    }
+    any = 0;
+#pragma unroll 8
+    for (uint32_t i = 0; i < 32; i++) {
+      const uint32_t wi = w0 + 32u * i + lane;
+      const uint32_t x = s_r[32u * i + lane] & (wi < F.gl.pw ? __ldg(F.gl.payload + wi) : 0u);
+      s_r[32u * i + lane] = x;
+      any |= x;
+    }
+  }
+  uint32_t n = 0;
+  if (any)
+    for (uint32_t i = 0; i < 32; i++) n += __popc(s_r[32u * i + lane]);
+  const uint32_t tot = __reduce_add_sync(kFull, n);
+  uint64_t off = 0;
+  if (lane == 0 && tot) off = atomicAdd(sc.counters + 1, (unsigned long long)tot);
+  off = __shfl_sync(kFull, off, 0);
+  const bool fits = off + tot <= arena_cap;
+  if (!fits && lane == 0) set_status(status, BP_ERR_CAPACITY);
+  if (fits && tot) {
+    uint32_t run = 0;
+    for (uint32_t i = 0; i < 32; i++) {
+      uint32_t x = s_r[32u * i + lane];
+      const uint32_t p = __popc(x);
+      uint32_t inc = p;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += y;
+      }
+      uint64_t pos = off + run + inc - p;
+      const uint32_t base = 32u * (w0 + 32u * i + lane);
+      while (x) {
+        sc.arena[pos++] = base + (uint32_t)(__ffs(x) - 1);
+        x &= x - 1;
+      }
+      run += __shfl_sync(kFull, inc, 31);
+    }
+  }
+  if (lane == 0) {
+    sc.item_q[item] = q;
+    sc.item_off[item] = fits ? off : ~0ull;
+    sc.item_cnt[item] = tot;
+  }
+  __syncwarp();
 }
 
 // At most 80 registers: 3 CTAs of 8 warps (or 6 of 4) per SM; more warps
 // in flight matter more here than the few values it would keep in registers.
+// Two instances: HYB = false for batches of compressed lists only, HYB =
+// true for batches with bitmap terms (hybrid index); the plan kernel records
+// which, and the other instance leaves at once.  The bitmap code would cost
+// the all-compressed kernel registers (measured: about 4 % of its speed).
+template <bool HYB>
 __global__ void __launch_bounds__(256, 3)
     q_main_kernel(const uint8_t *__restrict__ data, const bp_list *__restrict__ lists,
                               const uint64_t *__restrict__ toff, uint32_t nq, QScratch sc,
                               uint32_t max_items, uint64_t arena_cap, uint32_t chunk,
                               uint32_t dense_max, uint32_t *status) {
+  if ((sc.counters[2] != 0ull) != HYB) return;
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t *s_r = smem + w * kWarpSmemWords;
@@ -207,17 +348,23 @@ __global__ void __launch_bounds__(256, 3)
     const uint32_t c = item - sc.base[q];
     const uint64_t tb = toff[q];
     const uint32_t k = (uint32_t)(toff[q + 1] - tb);
-    GlView V1;
+    TermView V1;
     uint32_t scount = 0;
-    const uint32_t tv = term_view(data, lists, sc.sorted[tb], V1);
+    const uint32_t tv = term_view<HYB>(data, lists, sc.sorted[tb], V1);
+    if (HYB && tv == 0u && V1.bitmap) {
+      bitmap_and_item(data, lists, V1, sc.sorted + tb, k, c, q, item, sc, arena_cap, s_r, lane,
+                      status);
+      continue;
+    }
     if (tv == 0u) {
-      // the item's blocks of the shortest list; bit 4g+j of `alive`: value
-      // 32j + lane of block g is still a candidate
-      const uint32_t b0 = c * chunk, b1 = min(V1.nblocks, b0 + chunk);
-      const uint32_t ng = b1 > b0 ? b1 - b0 : 0u;
+      // the item's candidates, ascending, in s_r: `chunk` blocks of the
+      // shortest compressed list; bit 4g+j of `alive`: value 128g + 32j +
+      // lane is still a candidate
       uint32_t alive = 0;
+      const uint32_t b0 = c * chunk, b1 = min(V1.gl.nblocks, b0 + chunk);
+      const uint32_t ng = b1 > b0 ? b1 - b0 : 0u;
       for (uint32_t g = 0; g < ng; g++) {
-        const uint32_t cnt = gl_block_into(V1, b0 + g, s_r + 128u * g, lane, status);
+        const uint32_t cnt = gl_block_into(V1.gl, b0 + g, s_r + 128u * g, lane, status);
 #pragma unroll
         for (int j = 0; j < 4; j++)
           if ((uint32_t)(32 * j + lane) < cnt) alive |= 1u << (4 * g + j);
@@ -226,12 +373,16 @@ __global__ void __launch_bounds__(256, 3)
       // Set-vs-Set: the candidates go through the other lists in order, each
       // list searched run by run with its dense window moving forward
       for (uint32_t t = 1; t < k && __any_sync(kFull, alive != 0u); t++) {
-        GlView F;
-        const uint32_t tf = term_view(data, lists, sc.sorted[tb + t], F);
+        TermView F;
+        const uint32_t tf = term_view<HYB>(data, lists, sc.sorted[tb + t], F);
         if (tf != 0u) {
           if (lane == 0) set_status(status, tf);
           alive = 0;
           break;
+        }
+        if (HYB && F.bitmap) {
+          alive = bitmap_filter(F.gl.payload, F.gl.pw, s_r, ng, alive, lane);
+          continue;
         }
         FWin win = fwin_empty();
         for (uint32_t g = 0; g < ng; g++) {
@@ -250,7 +401,7 @@ __global__ void __launch_bounds__(256, 3)
           if (!__any_sync(kFull, (alive >> (4 * g)) & 0xFu)) continue;
           lo = __reduce_min_sync(kFull, lo);
           hi = __reduce_max_sync(kFull, hi);
-          gl_membership_win(F, v, valid, hit, lo, hi, s_f, win, lane, dense_max, status);
+          gl_membership_win(F.gl, v, valid, hit, lo, hi, s_f, win, lane, dense_max, status);
 #pragma unroll
           for (int j = 0; j < 4; j++)
             if (valid[j] && !hit[j]) alive &= ~(1u << (4 * g + j));
@@ -382,10 +533,10 @@ int g_main_smem_set = 0;
 
 // ---- host side -----------------------------------------------------------------------------------
 
-uint64_t query_items(uint64_t nmin) {
+uint64_t query_items_of(const bp_list &driver) {
   const uint32_t chunk = std::max<uint32_t>(1, std::min<uint32_t>(tuning().query_chunk_blocks,
                                                                  kMaxChunk));
-  return ((nmin + 127) / 128 + chunk - 1) / chunk;
+  return driver_items(driver, chunk);
 }
 
 size_t query_batch_scratch_for(uint64_t total_terms, uint32_t nq, uint64_t out_cap,
@@ -399,11 +550,15 @@ size_t query_batch_scratch_bytes(const bp_list *h_lists, uint32_t n_terms, const
                                                                  kMaxChunk));
   uint64_t items = 0;
   for (uint32_t q = 0; q < nq; q++) {
-    uint64_t nmin = UINT64_MAX;
+    uint64_t kmin = UINT64_MAX;
+    const bp_list *drv = nullptr;
     for (uint64_t i = h_term_off[q]; i < h_term_off[q + 1]; i++)
-      if (h_terms[i] < n_terms) nmin = std::min<uint64_t>(nmin, h_lists[h_terms[i]].n);
-    if (nmin == UINT64_MAX) continue;
-    items += ((nmin + 127) / 128 + chunk - 1) / chunk;
+      if (h_terms[i] < n_terms && svs_key(h_lists[h_terms[i]]) < kmin) {
+        kmin = svs_key(h_lists[h_terms[i]]);
+        drv = &h_lists[h_terms[i]];
+      }
+    if (!drv) continue;
+    items += driver_items(*drv, chunk);
   }
   return q_layout(h_term_off[nq], nq, out_cap, items).total + 4 * 256;
 }
@@ -426,24 +581,31 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
   const int threads = 32 * (int)warps;
   const size_t smem = sizeof(uint32_t) * kWarpSmemWords * warps;
   if (!g_main_smem_set) {
-    if (cudaFuncSetAttribute(q_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(q_main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess ||
+        cudaFuncSetAttribute(q_main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess)
       return BP_ERR_CUDA;
     g_main_smem_set = 1;
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_main_kernel, threads, smem) !=
-          cudaSuccess ||
+  int per_sm = 0, per_sm_h = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_main_kernel<false>, threads,
+                                                    smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  const int grid = per_sm * device_sm_count();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, q_main_kernel<true>, threads,
+                                                    smem) != cudaSuccess ||
+      per_sm_h < 1)
+    per_sm_h = 1;
+  const int grid = per_sm * device_sm_count(), grid_h = per_sm_h * device_sm_count();
   q_plan_kernel<<<(nq + 255) / 256, 256, 0, s>>>(lists, n_terms, terms, term_off, nq, sc, chunk,
                                                   status);
   scan_u32_kernel<<<1, 1024, 0, s>>>(sc.base, nq);
-  q_main_kernel<<<grid, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items, arena_cap,
-                                            chunk,
-                                            std::min<uint32_t>(tu.dense_blocks, kIxDenseMax),
-                                            status);
+  const uint32_t dense = std::min<uint32_t>(tu.dense_blocks, kIxDenseMax);
+  q_main_kernel<false><<<grid, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items,
+                                                   arena_cap, chunk, dense, status);
+  q_main_kernel<true><<<grid_h, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items,
+                                                    arena_cap, chunk, dense, status);
   const int cgrid = (int)std::min<uint64_t>((nq + 7) / 8, 65535);
   q_count_kernel<<<cgrid, 256, 0, s>>>(nq, sc, max_items, counts);
   scan_counts_kernel<<<1, 1024, 0, s>>>(counts, nq, out_off, out_cap, status);
@@ -500,6 +662,8 @@ int launch_query_one(const uint8_t *data, const bp_list *h_lists, const uint32_t
                      uint32_t k, uint32_t *out, uint64_t out_cap, uint32_t *count, void *scratch,
                      size_t scratch_bytes, uint32_t *status, cudaStream_t s) {
   if (scratch_bytes < query_one_scratch_bytes(h_lists, h_terms, k)) return BP_ERR_SCRATCH;
+  for (uint32_t i = 0; i < k; i++)  // the plain path decodes GL lists only
+    if (h_lists[h_terms[i]].layout != BP_LAYOUT_GPU) return BP_ERR_ARG;
   if (k == 0) {
     set_u32_kernel<<<1, 1, 0, s>>>(count, 0u);
     return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;

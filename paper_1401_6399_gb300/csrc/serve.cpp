@@ -125,13 +125,21 @@ bool bp_server::admit(Slot &s) {
     std::lock_guard<std::mutex> g(mu);
     while (!queue.empty() && take.size() < cfg.max_batch_queries) {
       const Pending &p = queue.front();
-      uint64_t nmin = 0;
+      uint64_t nmin = 0, qitems = 0;
       if (p.k) {
         nmin = UINT64_MAX;
-        for (uint32_t i = 0; i < p.k; i++) nmin = std::min<uint64_t>(nmin, h_lists[p.terms[i]].n);
+        const bp_list *drv = &h_lists[p.terms[0]];
+        for (uint32_t i = 0; i < p.k; i++) {
+          const bp_list &L = h_lists[p.terms[i]];
+          nmin = std::min<uint64_t>(nmin, L.n);
+          // the list that drives the query: compressed before bitmaps, then shortest
+          const bool lb = L.layout == BP_LAYOUT_BITMAP, db = drv->layout == BP_LAYOUT_BITMAP;
+          if (lb < db || (lb == db && L.n < drv->n)) drv = &L;
+        }
+        qitems = bp::query_items_of(*drv);
       }
       // memory this batch would need with p added
-      const uint64_t cap2 = cap + nmin, items2 = items + (p.k ? bp::query_items(nmin) : 0);
+      const uint64_t cap2 = cap + nmin, items2 = items + qitems;
       const size_t need = bp::query_batch_scratch_for(terms.size() + p.k,
                                                       (uint32_t)take.size() + 1,
                                                       std::max<uint64_t>(cap2, 1), items2);

@@ -8,6 +8,7 @@ import re
 import numpy as np
 import pytest
 
+import workloads as W
 from conftest import ROOT
 
 from paper_1401_6399_gb300.build import build
@@ -71,6 +72,74 @@ def test_encoder_kinds_match_oracle_bytes(orc, layout, kind):
         enc = np.frombuffer(want, np.uint8)
         assert capi.bp_stream_info(enc) == (x.size, layout)
         assert capi.bp_stream_kind(enc) == kind
+
+
+def test_encoder_any_order_fixed_widths(orc):
+    """BP_ENCODE_ANY_ORDER: any uint32 sequence (here stepped walks modulo
+    2^32 whose differences over 1..4 positions are below 2^b) encodes, with
+    every GL block of width exactly b, and the oracle decodes it back in both
+    layouts; without the flag the encoder rejects it."""
+    for b in (0, 1, 2, 3, 9, 16, 31, 32):
+        for kind in range(4):
+            x = W.stepped_walk(4096 * 2 + 200, b, 77 + b)
+            g = capi.bp_encode(x, capi.BP_LAYOUT_GPU, 1, kind | capi.BP_ENCODE_ANY_ORDER)
+            assert np.array_equal(orc.gl_decode(g.tobytes()), x)
+            info = orc.gl_info(g.tobytes())
+            assert info["payload_words"] == 4 * b * info["nblocks"]
+            p = capi.bp_encode(x, capi.BP_LAYOUT_PAPER, 1, kind | capi.BP_ENCODE_ANY_ORDER)
+            assert np.array_equal(orc.pl_decode(p.tobytes()), x)
+            assert capi.bp_stream_kind(g) == capi.bp_stream_kind(p) == kind
+            if b > 0:
+                with pytest.raises(capi.BPError) as e:
+                    capi.bp_encode(x, capi.BP_LAYOUT_GPU, 1, kind)
+                assert e.value.code == capi.BP_ERR_UNSORTED
+
+
+def test_pfor_encoder_matches_oracle_bytes(orc):
+    """S4-FastPFOR in the GP layout: the library's encoder writes the oracle's
+    bytes for every kind (lists with outliers, so blocks have exceptions),
+    and bp_stream_info / bp_stream_kind read the header."""
+    rng = np.random.default_rng(62)
+    for kind in range(4):
+        for n in (0, 1, 300, 4096 * 3 + 5, 70_000):
+            gaps = rng.geometric(0.25, n).astype(np.uint64)
+            jumps = rng.random(n) < 0.02
+            gaps[jumps] = rng.integers(1 << 8, 1 << 16, int(jumps.sum()))
+            x = np.cumsum(gaps).astype(np.uint32)
+            e = capi.bp_encode(x, capi.BP_LAYOUT_PFOR, 3, kind)
+            assert e.tobytes() == orc.gp_encode(x, kind)
+            assert capi.bp_stream_info(e) == (n, capi.BP_LAYOUT_PFOR)
+            assert capi.bp_stream_kind(e) == kind
+            assert e.size <= capi.bp_encode_bound(n, capi.BP_LAYOUT_PFOR)
+
+
+def test_hybrid_index_bitmaps():
+    """hyb+m2 index: a list whose average gap is at most B becomes a bitmap
+    (bit v set iff v is in the list; header {magic, 2, n, words}), the others
+    GL streams byte for byte as bp_encode writes them."""
+    rng = np.random.default_rng(5)
+    U = 1 << 16
+    lens = [0, 3, 100, U // 8 - 1, U // 8, U // 2, 4000]
+    xs = [np.sort(rng.choice(U, n, replace=False)).astype(np.uint32) for n in lens]
+    offs = np.zeros(len(xs) + 1, np.uint64)
+    np.cumsum([x.size for x in xs], out=offs[1:])
+    data, lists = capi.bp_index_encode_hybrid(np.concatenate(xs), offs, U, 8, nthreads=3)
+    for x, L in zip(xs, lists):
+        s = data[int(L["enc_offset"]):int(L["enc_offset"]) + int(L["enc_bytes"])]
+        if x.size * 8 >= U:
+            assert L["layout"] == capi.BP_LAYOUT_BITMAP
+            h = s[:16].view(np.uint32)
+            assert h[0] == 0x314D5042 and h[1] == 2 and h[2] == x.size
+            words = s[16:16 + 4 * int(h[3])].view(np.uint32)
+            bits = np.unpackbits(words.view(np.uint8), bitorder="little")
+            assert int(h[3]) * 32 >= U and int(h[3]) % 4 == 0
+            assert np.array_equal(np.flatnonzero(bits), x)
+        else:
+            assert L["layout"] == capi.BP_LAYOUT_GPU
+            assert s.tobytes() == capi.bp_encode(x, 1).tobytes()
+    with pytest.raises(capi.BPError):  # a value beyond the universe
+        bad = np.array([1, U + 5], np.uint32)
+        capi.bp_index_encode_hybrid(bad, np.array([0, 2], np.uint64), 16, 8)
 
 
 def test_encoder_rejects_unsorted_and_small_buffers():

@@ -166,6 +166,80 @@ def test_decode_batch_mixed_kinds(orc, layout):
     assert batch.sums().tolist() == [int(x.astype(np.uint64).sum()) for x in xs]
 
 
+def _outlier_list(rng, n):
+    """Sorted distinct values: small gaps with rare large jumps, so that
+    S4-FastPFOR blocks carry exceptions of several widths."""
+    gaps = rng.geometric(0.2, n).astype(np.uint64)
+    jumps = rng.random(n) < 0.02
+    gaps[jumps] = rng.integers(1 << 8, 1 << 22, int(jumps.sum()))
+    return (np.cumsum(gaps) % (1 << 32)).astype(np.uint32) if n else np.zeros(0, np.uint32)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_decode_pfor(orc, kind):
+    """S4-FastPFOR (GP layout) decodes bit-exactly against the oracle: edge
+    lengths, ragged tails, exceptions of many widths, the stream of the
+    library encoder equal to the oracle's byte for byte, decode and sum."""
+    rng = np.random.default_rng(60 + kind)
+    for n in (0, 1, 5, 127, 128, 129, 4095, 4096, 4097, 3 * 4096 + 200, 300_001):
+        x = np.unique(_outlier_list(rng, n))
+        enc = capi.bp_encode(x, capi.BP_LAYOUT_PFOR, 4, kind)
+        assert enc.tobytes() == orc.gp_encode(x, kind)
+        want = orc.gp_decode(enc.tobytes())
+        assert np.array_equal(want, x)
+        got = api.as_u32(api.decode(api.to_device(enc), capi.BP_LAYOUT_PFOR, x.size))
+        assert np.array_equal(got, want), (kind, n)
+        assert (api.decode_sum(api.to_device(enc), capi.BP_LAYOUT_PFOR, x.size) ==
+                int(x.astype(np.uint64).sum()) % (1 << 64))
+
+
+def test_decode_pfor_batch_widths_and_order(orc):
+    """One batch of GP lists: every width 0..32 (stepped walks modulo 2^32 with
+    planted outliers, BP_ENCODE_ANY_ORDER), all kinds, ragged lengths; pages
+    too large for the shared-memory stage take the global-memory path."""
+    xs, encs = [], []
+    rng = np.random.default_rng(61)
+    for b in range(33):
+        kind = b % 4
+        n = [4096, 4096 * 2 + 77, 129, 1, 0, 6000][b % 6]
+        x = W.stepped_walk(n, b, 1200 + b)
+        if n > 10:  # outliers: a few values moved far away
+            idx = rng.choice(n, max(1, n // 100), replace=False)
+            x[idx] = rng.integers(0, 1 << 32, idx.size, dtype=np.uint64).astype(np.uint32)
+        e = capi.bp_encode(x, capi.BP_LAYOUT_PFOR, 1, kind | capi.BP_ENCODE_ANY_ORDER)
+        assert np.array_equal(orc.gp_decode(e.tobytes()), x)
+        xs.append(x)
+        encs.append(e)
+    batch = api.ListBatch(encs, [x.size for x in xs], capi.BP_LAYOUT_PFOR)
+    assert np.array_equal(api.as_u32(batch.decode()), np.concatenate(xs))
+    assert batch.sums().tolist() == [int(x.astype(np.uint64).sum()) % (1 << 64) for x in xs]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_decode_ablation_any_width_and_order(orc, mode):
+    """bp_decode_ablation (prefix integrated or as a separate pass) and
+    bp_decode_batch agree with the oracle on GL streams of every kind whose
+    blocks all have width b (stepped walks modulo 2^32, encoded with
+    BP_ENCODE_ANY_ORDER), ragged lengths, one batch of lists."""
+    xs, encs = [], []
+    for b in (0, 1, 2, 3, 7, 8, 13, 16, 24, 31, 32):
+        for kind in range(4):
+            n = [4096, 4096 * 3 + 77, 129, 1, 0][(b + kind) % 5]
+            x = W.stepped_walk(n, b, 900 + 4 * b + kind)
+            e = capi.bp_encode(x, capi.BP_LAYOUT_GPU, 1, kind | capi.BP_ENCODE_ANY_ORDER)
+            assert np.array_equal(orc.gl_decode(e.tobytes()), x)
+            xs.append(x)
+            encs.append(e)
+    batch = api.ListBatch(encs, [x.size for x in xs], capi.BP_LAYOUT_GPU)
+    want = np.concatenate(xs)
+    out = torch.full((max(batch.total_n, 1),), -1, dtype=torch.int32, device="cuda")
+    st = api.status_tensor()
+    batch.ablation_into(out, st, mode)
+    api.check_status(st, "bp_decode_ablation")
+    assert np.array_equal(api.as_u32(out[:batch.total_n]), want)
+    assert np.array_equal(api.as_u32(batch.decode()), want)
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_decode_batch_host(orc, layout):
     """bp_decode_batch_host from pinned host memory to pinned host memory.

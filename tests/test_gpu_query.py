@@ -169,3 +169,45 @@ def test_full_size_index_sampled(orc):
     for q in range(0, 100_000, 997):
         r = answer(q).astype(np.int64)
         assert np.all(np.diff(r) > 0)
+
+
+@pytest.fixture(scope="module")
+def zipf_data():
+    lens = W.zipf_lengths(1 << 13, 20_000_000, 1 << 20).astype(np.int64)
+    lens[5] = 0
+    lens[17] = 1
+    vals, offs = W.many("clustered", lens, 0, 1 << 22, 0x4100)
+    return vals, offs
+
+
+@pytest.mark.parametrize("B", [8, 32, 1 << 22])
+def test_hybrid_index_matches_svs(orc, zipf_data, B):
+    """hyb+m2: lists with average gap <= B are bitmaps over [0, 2^22); the
+    answers are the oracle's Set-vs-Set whatever mix of bitmaps and GL lists a
+    query has (B = 2^22: every non-empty list is a bitmap)."""
+    vals, offs = zipf_data
+    U = 1 << 22
+    idx = api.Index(vals, offs, hybrid_B=B, universe=U)
+    lens = np.diff(offs)
+    is_bm = idx.h_lists["layout"] == capi.BP_LAYOUT_BITMAP
+    assert np.array_equal(is_bm, lens.astype(np.uint64) * B >= U)
+    assert is_bm.any()
+    terms, toff = queries(lens, 1500, 0x4C00 + B)
+    nbm = [int(is_bm[terms[int(toff[q]):int(toff[q + 1])]].sum()) for q in range(toff.size - 1)]
+    kq = np.diff(toff)
+    if B < U:
+        assert any(0 < m < k for m, k in zip(nbm, kq))  # mixed queries
+    assert any(m == k and k > 1 for m, k in zip(nbm, kq))  # all-bitmap queries
+    res = idx.query_batch(terms, toff)
+    check_all(orc, idx, vals, offs, terms, toff, res)
+    # hand-picked: bitmap alone, bitmap twice, bitmap with the empty list and
+    # the single-value list, the longest lists together
+    big = np.argsort(lens)[::-1][:4].astype(np.uint32)
+    qs = [[big[0]], [big[0], big[0]], [big[0], 5], [17, big[1]], list(big), [big[3], 3, big[2]]]
+    terms = np.array([t for q in qs for t in q], np.uint32)
+    toff = np.cumsum([0] + [len(q) for q in qs]).astype(np.uint64)
+    check_all(orc, idx, vals, offs, terms, toff, idx.query_batch(terms, toff))
+    if is_bm[big[0]]:
+        with pytest.raises(capi.BPError) as e:  # the plain path takes GL lists only
+            idx.query_one(np.array([big[0], 3], np.uint32))
+        assert e.value.code == capi.BP_ERR_ARG

@@ -78,3 +78,26 @@ def test_oversized_query_is_rejected_alone(orc, index):
     assert res[1][2] == capi.BP_ERR_SCRATCH
     assert res[2][2] == capi.BP_OK
     assert np.array_equal(res[2][5], svs(orc, vals, offs, small))
+
+
+def test_hybrid_index_served(orc):
+    """The engine over a hybrid (hyb+m2) index: lists with average gap <= 16
+    are bitmaps; answers of an open-loop mix equal the oracle's."""
+    lens = W.zipf_lengths(1 << 12, 8_000_000, 1 << 20)
+    vals, offs = W.many("clustered", lens, 0, 1 << 22, 0x5100)
+    idx = api.Index(vals, offs, hybrid_B=16, universe=1 << 22)
+    assert (idx.h_lists["layout"] == capi.BP_LAYOUT_BITMAP).any()
+    terms, toff = W.queries(np.diff(offs), 300, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5101)
+    n = toff.size - 1
+    srv = api.Server(idx, slots=4, max_batch_queries=64, max_terms=8, slot_bytes=256 << 20)
+    try:
+        srv.replay(np.arange(n), terms, toff, W.poisson_arrivals(100_000.0, n, 0x5102))
+        srv.drain()
+        got = {tag: (st, ans) for (tag, cnt, st, t0, t1, ans) in srv.poll()}
+    finally:
+        srv.close()
+    assert sorted(got) == list(range(n))
+    for q in range(n):
+        st, ans = got[q]
+        assert st == capi.BP_OK
+        assert np.array_equal(ans, svs(orc, vals, offs, terms[int(toff[q]):int(toff[q + 1])])), q

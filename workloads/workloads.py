@@ -129,6 +129,19 @@ def queries(lens, nq: int, weights, tmin: int, seed: int):
     return terms[: int(off[-1])], off
 
 
+def stepped_walk(n: int, b: int, seed: int, every: int = 4) -> np.ndarray:
+    """A random walk modulo 2^32 that moves only at positions i = 0 mod
+    `every`, by a step drawn uniformly from [0, 2^b); it stays put
+    elsewhere.  Any `every` consecutive steps contain one move, so every
+    difference x[i] - x[i-k] for 1 <= k <= `every` is below 2^b.  Not
+    strictly increasing (equal neighbours, wrap-around)."""
+    rng = np.random.default_rng(seed)
+    steps = np.zeros(n, np.uint64)
+    m = (n + every - 1) // every
+    steps[::every] = rng.integers(0, 1 << b, m, dtype=np.uint64) if b else 0
+    return (np.cumsum(steps, dtype=np.uint64) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
 def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     """Arrival times in seconds of an open-loop Poisson process."""
     rng = np.random.default_rng(seed)
