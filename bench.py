@@ -52,6 +52,10 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true", help="skip secondary measurements")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--queries-only", action="store_true",
+                   help="run only the batched-query measurement (for profiling)")
+    p.add_argument("--query-scale", type=int, default=1,
+                   help="with --queries-only: index and batch this many times smaller")
     return p.parse_args()
 
 
@@ -517,22 +521,58 @@ def graph_batch(idx, terms, toff, total, stream, reps):
     return e0.elapsed_time(e1) / reps, out[:total], out_off, counts
 
 
-def batched_queries(stream, reps: int, plain_queries: int):
+def query_alg_bytes(idx, vals, offs, terms, toff, sample: int, seed: int) -> float:
+    """Algorithmic bytes of one fused query, averaged over `sample` queries
+    of the batch, computed on the host by Set-vs-Set in the kernel's order:
+    the shortest list's whole stream; for every other list, the payload and
+    skip-header entry (first value, width byte) of each block that holds a
+    still-alive candidate; 4 bytes per answer value."""
+    rng = np.random.default_rng(seed)
+    nq = toff.size - 1
+    L = idx.h_lists
+    data = idx.host_data
+    total = 0
+    for q in rng.choice(nq, min(sample, nq), replace=False):
+        t = [int(u) for u in terms[int(toff[q]):int(toff[q + 1])]]
+        order = sorted(t, key=lambda u: (int(L["n"][u]), u))
+        drv = order[0]
+        total += int(L["enc_bytes"][drv])
+        cand = vals[int(offs[drv]):int(offs[drv + 1])]
+        for u in order[1:]:
+            if cand.size == 0:
+                break
+            f = vals[int(offs[u]):int(offs[u + 1])]
+            blk = np.unique(np.searchsorted(f[::128], cand, side="right") - 1)
+            blk = blk[blk >= 0]
+            eo = int(L["enc_offset"][u])
+            off_bw = int(data[eo + 32:eo + 36].view(np.uint32)[0])
+            bw = data[eo + off_bw + blk].astype(np.int64)
+            total += int(16 * bw.sum()) + 5 * int(blk.size)
+            pos = np.minimum(np.searchsorted(f, cand), max(f.size - 1, 0))
+            cand = cand[f[pos] == cand] if f.size else cand[:0]
+        total += 4 * int(cand.size)
+    return total / min(sample, nq)
+
+
+def batched_queries(stream, reps: int, plain_queries: int, scale: int = 1,
+                    hybrid_bs=(8, 16, 32)):
     """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
     2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
     100,000 queries of 2-5 terms drawn in proportion to list length.  One
-    autotuned, CUDA-graph-captured bp_query_batch vs bp_query_one per query."""
+    autotuned, CUDA-graph-captured bp_query_batch vs bp_query_one per query.
+    scale > 1 divides the terms, postings, cap and queries by it (a small
+    case of the same shape, for profiling)."""
     import torch
     import workloads as W
     from paper_1401_6399_gb300 import api, autotune, capi
     t0 = time.time()
-    lens = W.zipf_lengths(1 << 19, 1_500_000_000, 1 << 24)
+    lens = W.zipf_lengths((1 << 19) // scale, 1_500_000_000 // scale, (1 << 24) // scale)
     vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
     idx = api.Index(vals, offs)
-    terms, toff = W.queries(lens, 100_000, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
+    terms, toff = W.queries(lens, 100_000 // scale, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
     setup_s = time.time() - t0
     # autotune on a 5,000-query sample of the batch
-    sample_n = 5000
+    sample_n = min(5000, toff.size - 1)
     tuned = autotune.tune_queries(idx, terms[: int(toff[sample_n])], toff[: sample_n + 1],
                                   reps=2)
     # exact output size, then a graph-captured batch
@@ -546,7 +586,7 @@ def batched_queries(stream, reps: int, plain_queries: int):
     # the same batch over hybrid indexes (hyb+m2): lists with average gap <= B
     # stored as bitmaps of 2^25 bits; the answers must be the same
     hybrid = {}
-    for B in (8, 16, 32):
+    for B in hybrid_bs:
         h0 = time.time()
         hidx = api.Index(vals, offs, hybrid_B=B, universe=1 << 25)
         enc_s = time.time() - h0
@@ -599,13 +639,20 @@ def batched_queries(stream, reps: int, plain_queries: int):
         assert torch.equal(got, want), f"batched and plain answers differ for query {q}"
     qps = nq / (ms * 1e-3)
     qps_plain = qn / (ms_plain * 1e-3)
+    # algorithmic bytes per query on a sample of 300 queries -> HBM fraction
+    apq = query_alg_bytes(idx, vals, offs, terms, toff, 300, 0x4A10)
+    peak, peak_kind = load_peaks()
+    alg_gbs = apq * nq / (ms * 1e-3) / 1e9
     batched_queries.index = (idx, lens)  # reused by the serving measurement
     return {"queries": nq, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
             "plain_queries_timed": qn, "plain_queries_per_s": round(qps_plain, 1),
             "speedup_vs_plain": round(qps / qps_plain, 1), "answer_values": total,
             "index_postings": int(lens.sum()), "index_bytes": idx.compressed_bytes,
             "bits_per_posting": round(8 * idx.compressed_bytes / int(lens.sum()), 3),
-            "tuned": tuned["best"], "setup_s": round(setup_s, 1), "hybrid": hybrid}
+            "tuned": tuned["best"], "setup_s": round(setup_s, 1),
+            "alg_bytes_per_query_sampled": round(apq, 1),
+            "alg_gbs": round(alg_gbs, 1), "hbm_frac": round(alg_gbs / peak, 4),
+            "hbm_peak": f"{peak} GB/s ({peak_kind})", "hybrid": hybrid}
 
 
 def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
@@ -914,6 +961,17 @@ def main():
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.queries_only:
+        # the batched-query measurement alone, on an index `--query-scale`
+        # times smaller (for profiling its kernels); one JSON line
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        stream = torch.cuda.Stream()
+        res = batched_queries(stream, reps=args.steps, plain_queries=100,
+                              scale=args.query_scale, hybrid_bs=())
+        print(json.dumps({"batched_queries": res, "scale": args.query_scale}), flush=True)
         return
     run_ours(args, rank, world, local)
 

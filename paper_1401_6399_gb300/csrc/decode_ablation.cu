@@ -7,9 +7,10 @@
 // memory and the prefix then runs over it as a second pass.  Both variants
 // here are one list-major kernel of identical structure; the two-pass one
 // stores every block's deltas to a buffer of 128 words of shared memory per
-// warp (the nearest memory, as the paper's block buffer sits in L1), reads
-// them back and then prefixes and stores the values.  Any kind of
-// differential coding.
+// warp (the nearest memory, as the paper's block buffer sits in L1; the
+// j-th delta of lane l at word 32j + l, free of bank conflicts), reads them
+// back and then prefixes and stores the values.  Any kind of differential
+// coding.
 #include "decode.h"
 #include "bulk.cuh"
 #include "gl_block.cuh"
@@ -81,10 +82,10 @@ __device__ __forceinline__ void ablation_unit(const GlView &v, const SuperInfo &
     block_deltas(b, words(woff), lane, d);
     if (MODE == 1) {
 #pragma unroll
-      for (int t = 0; t < 4; t++) st_shared_volatile(s_blk + gl_pos(lane, t), d[t]);
+      for (int t = 0; t < 4; t++) st_shared_volatile(s_blk + 32 * t + lane, d[t]);
       __syncwarp();
 #pragma unroll
-      for (int t = 0; t < 4; t++) d[t] = ld_shared_volatile(s_blk + gl_pos(lane, t));
+      for (int t = 0; t < 4; t++) d[t] = ld_shared_volatile(s_blk + 32 * t + lane);
       __syncwarp();
     }
     uint32_t x[4], ctot;

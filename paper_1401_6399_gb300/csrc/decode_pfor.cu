@@ -152,11 +152,18 @@ __device__ __forceinline__ bool gp_page(const GpView &v, uint32_t q, int lane, P
   return true;
 }
 
+// Slot of block position p in a per-warp patch array: lane l's four
+// positions 16c + 4t + s (l = 8s + c) sit at 32t + l, so the lanes' reads
+// of one t fall in 32 different banks.
+__device__ __forceinline__ uint32_t patch_slot(uint32_t p) {
+  return 32u * ((p >> 2) & 3u) + 8u * (p & 3u) + (p >> 4);
+}
+
 // The blocks of one page.  Exceptions are patched through a per-warp
 // array of 128 patch words in shared memory, zero between blocks: the lanes
 // that take an exception (one each) write its high bits, shifted to above
-// the low b' bits, at its position; every lane ORs in the words at its four
-// positions; the exception lanes zero their words again.
+// the low b' bits, at its position's slot; every lane ORs in the words of its
+// four positions; the exception lanes zero their words again.
 template <bool SUM, int KIND, class P>
 __device__ __forceinline__ void gp_decode_page(const GpView &v, const PageInfo &pi, uint32_t q,
                                                const P &pg, uint32_t *s_patch, int lane,
@@ -184,14 +191,14 @@ __device__ __forceinline__ void gp_decode_page(const GpView &v, const PageInfo &
           uint64_t hv = pg.word(k) >> o;
           if (o + w > 32u) hv |= (uint64_t)pg.word(k + 1) << (32u - o);
           const uint32_t high = (uint32_t)hv & (w >= 32u ? 0xFFFFFFFFu : (1u << w) - 1u);
-          if (p < 128u) s_patch[p] = high << bp;  // bp < 32 when there are exceptions
+          if (p < 128u) s_patch[patch_slot(p)] = high << bp;  // bp < 32 here
           else set_status(status, BP_ERR_CORRUPT);
         }
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 4; t++) d[t] |= s_patch[gl_pos(lane, t)];
+        for (int t = 0; t < 4; t++) d[t] |= s_patch[32 * t + lane];
         __syncwarp();
-        if (p < 128u) s_patch[p] = 0u;
+        if (p < 128u) s_patch[patch_slot(p)] = 0u;
         __syncwarp();
       }
     }

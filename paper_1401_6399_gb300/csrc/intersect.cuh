@@ -62,15 +62,31 @@ __device__ __forceinline__ int64_t lane_ubound(const uint32_t *__restrict__ a, i
   return L - 1;
 }
 
-// Is v among s[0..len)?  (s ascending, in shared memory)
-__device__ __forceinline__ bool smem_contains(const uint32_t *s, uint32_t len, uint32_t v) {
-  uint32_t L = 0, H = len;
-  while (L < H) {
-    const uint32_t mid = (L + H) >> 1;
-    if (s[mid] < v) L = mid + 1;
-    else H = mid;
+// Which of a lane's four values are among s[0..len) (s ascending, in shared
+// memory): four lower-bound searches by halving, interleaved so that their
+// shared-memory loads overlap; the number of steps depends only on len (the
+// same in every lane).
+__device__ __forceinline__ void smem_contains4(const uint32_t *s, uint32_t len,
+                                               const uint32_t v[4], const bool valid[4],
+                                               bool hit[4]) {
+  if (len == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) hit[k] = false;
+    return;
   }
-  return L < len && s[L] == v;
+  uint32_t base[4] = {0u, 0u, 0u, 0u};
+  uint32_t n = len;
+  while (n > 1) {  // invariant: the lower bound of v[k] lies in [base[k], base[k] + n]
+    const uint32_t half = n >> 1;
+#pragma unroll
+    for (int k = 0; k < 4; k++) base[k] = (s[base[k] + half - 1] < v[k]) ? base[k] + half : base[k];
+    n -= half;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint32_t lb = base[k] + (s[base[k]] < v[k] ? 1u : 0u);
+    hit[k] = valid[k] && lb < len && s[lb] == v[k];
+  }
 }
 
 __device__ __forceinline__ bool gmem_contains(const uint32_t *__restrict__ a, int64_t lo,
@@ -225,8 +241,7 @@ __device__ __forceinline__ void gl_membership(const GlView &f, const uint32_t v[
       if (c < 128u) break;  // only the last block of f is short
     }
     __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 4; k++) hit[k] = valid[k] && smem_contains(smem, len, v[k]);
+    smem_contains4(smem, len, v, valid, hit);
     __syncwarp();
     return;
   }
@@ -252,8 +267,7 @@ __device__ __forceinline__ void raw_membership(const uint32_t *__restrict__ f, u
   if (span <= 128ull * dense_max) {
     for (uint32_t i = lane; i < span; i += 32) smem[i] = __ldg(f + lo + i);
     __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 4; k++) hit[k] = valid[k] && smem_contains(smem, (uint32_t)span, v[k]);
+    smem_contains4(smem, (uint32_t)span, v, valid, hit);
     __syncwarp();
     return;
   }
@@ -354,8 +368,7 @@ __device__ __forceinline__ void gl_membership_win(const GlView &f, const uint32_
     win.len = len;
     win.first_lo = __ldg(f.first + klo);
   }
-#pragma unroll
-  for (int k = 0; k < 4; k++) hit[k] = valid[k] && smem_contains(smem, win.len, v[k]);
+  smem_contains4(smem, win.len, v, valid, hit);
   __syncwarp();
 }
 
