@@ -242,6 +242,42 @@ __device__ __forceinline__ void gl_block_values(int b, const uint32_t *__restric
   gl_block_values_from(b, GlobalWords{w}, F, lane, x);
 }
 
+// The same with the width known only at run time: no per-width code, so a
+// few dozen instructions instead of 33 specialised routines -- for kernels
+// whose instruction footprint matters more than the last shift (the
+// intersections decode blocks at several call sites).  Lane l's value j
+// sits at bit 4bl + jb of the block's words w[0..4b).
+__device__ __forceinline__ void gl_block_values_rt(uint32_t b, const uint32_t *__restrict__ w,
+                                                   uint32_t F, int lane, uint32_t x[4]) {
+  uint32_t d[4] = {0u, 0u, 0u, 0u};
+  if (b != 0u) {
+    const uint32_t mask = b >= 32u ? 0xFFFFFFFFu : (1u << b) - 1u;
+    uint32_t bit = 4u * b * (uint32_t)lane;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const uint32_t k = bit >> 5, r = bit & 31u;
+      const uint32_t lo = __ldg(w + k);
+      const uint32_t hi = (r + b > 32u) ? __ldg(w + k + 1) : 0u;
+      d[j] = __funnelshift_r(lo, hi, r) & mask;
+      bit += b;
+    }
+  }
+  x[0] = d[0];
+  x[1] = x[0] + d[1];
+  x[2] = x[1] + d[2];
+  x[3] = x[2] + d[3];
+  const int c = lane & 7;
+  uint32_t incl = x[3];
+#pragma unroll
+  for (int dd = 1; dd < 8; dd <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, dd, 8);
+    if (c >= dd) incl += t;
+  }
+  const uint32_t base = F + (incl - x[3]);
+#pragma unroll
+  for (int j = 0; j < 4; j++) x[j] += base;
+}
+
 // In-block position of x[j] for `lane`.
 __device__ __forceinline__ int gl_pos(int lane, int j) { return 16 * (lane & 7) + 4 * j + (lane >> 3); }
 

@@ -102,7 +102,11 @@ __device__ __forceinline__ bool gmem_contains(const uint32_t *__restrict__ a, in
 
 // Decode block k of GL list v into dst[0..128) (natural order) with the
 // whole warp; returns the number of real values in it (0 if the block's
-// header is inconsistent, which is also recorded as BP_ERR_CORRUPT).
+// header is inconsistent, which is also recorded as BP_ERR_CORRUPT).  The
+// width is handled at run time (gl_block_values_rt): the intersection
+// kernels decode blocks at several call sites, and 33 specialised unpackers
+// per site made the batched-query kernel stall on instruction fetch
+// (measured: +9 % queries/s with the run-time width).
 __device__ __forceinline__ uint32_t gl_block_into(const GlView &v, uint32_t k, uint32_t *dst,
                                                   int lane, uint32_t *status) {
   const uint32_t q = k >> 5, j = k & 31u, k0 = q << 5;
@@ -115,7 +119,7 @@ __device__ __forceinline__ uint32_t gl_block_into(const GlView &v, uint32_t k, u
     return 0;
   }
   uint32_t x[4];
-  gl_block_values((int)b, v.payload + woff, __ldg(v.first + k), lane, x);
+  gl_block_values_rt(b, v.payload + woff, __ldg(v.first + k), lane, x);
 #pragma unroll
   for (int t = 0; t < 4; t++) dst[gl_pos(lane, t)] = x[t];
   return min(128u, v.n - 128u * k);
