@@ -83,12 +83,27 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, value: float) -> float:
+    """The largest of the ranks' values (the slowest rank's time), on the
+    GPU under NCCL, on the host under gloo."""
     if dist is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Seed base of a rank's lists: every rank decodes lists of its own
+    (weak scaling, no data exchanged)."""
+    return SEED_BASE + 4096 * rank
+
+
+def whole_job_rate(world: int, ints_per_rank: int, ms_max: float) -> float:
+    """Gint/s of the whole job: all ranks' integers over the slowest rank's
+    time per step."""
+    return world * ints_per_rank / (ms_max * 1e-3) / 1e9
 
 
 # ---- clocks --------------------------------------------------------------------------
@@ -708,7 +723,7 @@ def run_ours(args, rank, world, local):
 
     n = 1 << args.log2n
     L = args.lists
-    seed = SEED_BASE + 4096 * rank
+    seed = rank_seed(rank)
     lists = make_lists("uniform", L, n, UNIVERSE, seed)
     layout = {"paper": capi.BP_LAYOUT_PAPER, "gpu": capi.BP_LAYOUT_GPU,
               "pfor": capi.BP_LAYOUT_PFOR}[args.layout]
@@ -764,7 +779,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.summary(w0, w1)
     assert int(status.item()) == 0
 
-    value = world * total_n / (ms * 1e-3) / 1e9  # Gint/s over all ranks
+    value = whole_job_rate(world, total_n, ms)  # Gint/s over all ranks
     comp_bytes = batch.compressed_bytes
     alg_bytes = comp_bytes + 4 * total_n  # per launch (one launch per step)
     peak, peak_kind = load_peaks()
