@@ -342,6 +342,40 @@ def test_corrupt_streams_record_status():
     assert _status_of(gl, 1, x.size, cap=x.size - 1)[0] == capi.BP_ERR_CAPACITY
 
 
+def test_corrupt_pfor_streams_record_status():
+    """GP streams with an inconsistent meta entry, page offset, position byte,
+    magic or length record BP_ERR_CORRUPT (every access stays inside the
+    stream: the page's words are checked against its meta entries first)."""
+    rng = np.random.default_rng(70)
+    x = np.unique(_outlier_list(rng, 20_000))
+    gp = capi.bp_encode(x, capi.BP_LAYOUT_PFOR, 1).copy()
+    L = capi.BP_LAYOUT_PFOR
+    assert _status_of(gp, L, x.size) == (capi.BP_OK, capi.BP_OK)
+    h = gp[:64].view(np.uint32)
+    off_spo, off_meta, off_payload = int(h[7]), int(h[8]), int(h[9])
+    meta = gp[off_meta:off_meta + 4 * int(h[3])].reshape(-1, 4)
+    k = int(np.flatnonzero(meta[:, 2])[0])        # a block with exceptions
+    bad = gp.copy()
+    bad[off_meta + 4 * k + 1] = 40                # b' + (b - b') > 32
+    assert _status_of(bad, L, x.size)[1] == capi.BP_ERR_CORRUPT
+    bad = gp.copy()
+    bad[off_meta + 4 * k + 0] += 1                # page words no longer match
+    assert _status_of(bad, L, x.size)[1] == capi.BP_ERR_CORRUPT
+    bad = gp.copy()
+    bad[off_spo + 4:off_spo + 8] = np.array([0xFFFFFF00], np.uint32).view(np.uint8)
+    assert _status_of(bad, L, x.size)[1] == capi.BP_ERR_CORRUPT
+    # the first exception position byte of page 0 set beyond the block
+    low = 4 * int(meta[:32, 0].astype(np.int64).sum())
+    bad = gp.copy()
+    bad[off_payload + 4 * low] = 200
+    assert _status_of(bad, L, x.size)[1] == capi.BP_ERR_CORRUPT
+    bad = gp.copy()
+    bad[0] ^= 1
+    assert _status_of(bad, L, x.size)[1] == capi.BP_ERR_CORRUPT
+    assert _status_of(gp[:-16], L, x.size)[1] == capi.BP_ERR_CORRUPT
+    assert _status_of(gp, L, x.size - 1)[1] == capi.BP_ERR_CORRUPT
+
+
 def test_decode_is_deterministic_across_streams():
     x = W.clustered(300_000, 0, 1 << 28, 5)
     for layout in LAYOUTS:
