@@ -189,38 +189,43 @@ __device__ __forceinline__ bool column_lookup(const GlView &v, uint32_t k, uint3
 
 // Resolve the probes of a warp (lane holds positions 32k + lane; cb[k] its
 // candidate block, < klo when there is none) eight at a time: probe i of a
-// round goes to lanes 4i..4i+3.
+// round goes to lanes 4i..4i+3.  The loop over the lane's four registers is
+// kept rolled (the values are picked by selects): one copy of the probe
+// code instead of four keeps the calling kernels' code small.
 __device__ __forceinline__ void lookup_probes(const GlView &f, const uint32_t v[4],
                                               const bool valid[4], const int64_t cb[4],
                                               int64_t klo, bool hit[4], int lane,
                                               uint32_t *status) {
-#pragma unroll
+  uint32_t hits = 0;
+#pragma unroll 1
   for (int k = 0; k < 4; k++) {
-    hit[k] = false;
-    const bool want = valid[k] && cb[k] >= klo;
-    uint32_t pend = __ballot_sync(kFull, want);  // probes of this register
-    while (pend) {                                // up to 8 per round
+    const uint32_t vk = k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
+    const int64_t ck = k == 0 ? cb[0] : k == 1 ? cb[1] : k == 2 ? cb[2] : cb[3];
+    const bool ok = k == 0 ? valid[0] : k == 1 ? valid[1] : k == 2 ? valid[2] : valid[3];
+    uint32_t pend = __ballot_sync(kFull, ok && ck >= klo);  // probes of this register
+    while (pend) {                                           // up to 8 per round
       // the i-th set bit of pend goes to lane group i
       const int g = lane >> 2;
       uint32_t m = pend;
       for (int i = 0; i < g && m; i++) m &= m - 1;
       const bool act = m != 0;
       const int src = act ? __ffs(m) - 1 : 0;
-      const uint32_t pv = __shfl_sync(kFull, v[k], src);
-      const uint32_t pb = (uint32_t)__shfl_sync(kFull, (uint32_t)cb[k], src);
+      const uint32_t pv = __shfl_sync(kFull, vk, src);
+      const uint32_t pb = (uint32_t)__shfl_sync(kFull, (uint32_t)ck, src);
       const bool found = column_lookup(f, pb, pv, act, lane, status);
       // hand each answer back to the lane that owns the probe
       const uint32_t ans = __ballot_sync(kFull, act && (lane & 3) == 0 && found);
       // lane L owns probe number r = popc(pend & lanemask_lt(L)) of this round
-      const uint32_t mine = pend & (1u << lane);
-      if (mine) {
+      if (pend & (1u << lane)) {
         const uint32_t r = __popc(pend & ((1u << lane) - 1u));
-        if (r < 8u) hit[k] = (ans >> (4u * r)) & 1u;
+        if (r < 8u && ((ans >> (4u * r)) & 1u)) hits |= 1u << k;
       }
       // drop the (up to 8) probes handled this round
       for (int i = 0; i < 8 && pend; i++) pend &= pend - 1;
     }
   }
+#pragma unroll
+  for (int k = 0; k < 4; k++) hit[k] = (hits >> k) & 1u;
 }
 
 // Membership of the warp's values (lane holds positions 32k + lane, k < 4,
