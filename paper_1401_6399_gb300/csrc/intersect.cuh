@@ -50,16 +50,27 @@ __device__ __forceinline__ int64_t warp_ubound(const uint32_t *__restrict__ a, u
   return (int64_t)lo - 1 + __popc(__ballot_sync(kFull, le));
 }
 
-// Largest k in [lo, hi] with a[k] <= v, or lo-1 (per lane).
-__device__ __forceinline__ int64_t lane_ubound(const uint32_t *__restrict__ a, int64_t lo,
-                                               int64_t hi, uint32_t v) {
-  int64_t L = lo, H = hi + 1;  // first index with a > v in [L, H]
-  while (L < H) {
-    const int64_t mid = (L + H) >> 1;
-    if (__ldg(a + mid) <= v) L = mid + 1;
-    else H = mid;
+// For each of a lane's four values, the largest k in [lo, hi] with
+// a[k] <= v[k] (lo - 1 if none, or if !valid[k]): four searches by halving
+// over the same range, interleaved so that their global loads overlap; the
+// range is the same in every lane.
+__device__ __forceinline__ void lane_ubound4(const uint32_t *__restrict__ a, int64_t lo,
+                                             int64_t hi, const uint32_t v[4],
+                                             const bool valid[4], int64_t cb[4]) {
+  int64_t base[4] = {lo, lo, lo, lo};
+  int64_t n = hi - lo + 1;  // the upper bound of v[k] lies in [base[k], base[k] + n]
+  while (n > 1) {
+    const int64_t half = n >> 1;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      base[k] = (__ldg(a + base[k] + half - 1) <= v[k]) ? base[k] + half : base[k];
+    n -= half;
   }
-  return L - 1;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int64_t ub = base[k] + ((n == 1 && __ldg(a + base[k]) <= v[k]) ? 1 : 0);
+    cb[k] = valid[k] ? ub - 1 : lo - 1;
+  }
 }
 
 // Which of a lane's four values are among s[0..len) (s ascending, in shared
@@ -256,8 +267,7 @@ __device__ __forceinline__ void gl_membership(const GlView &f, const uint32_t v[
   }
   // sparse regime: every value looks up its own candidate block
   int64_t cb[4];
-#pragma unroll
-  for (int k = 0; k < 4; k++) cb[k] = valid[k] ? lane_ubound(f.first, klo, khi, v[k]) : klo - 1;
+  lane_ubound4(f.first, klo, khi, v, valid, cb);
   lookup_probes(f, v, valid, cb, klo, hit, lane, status);
 }
 
@@ -342,9 +352,7 @@ __device__ __forceinline__ void gl_membership_win(const GlView &f, const uint32_
     const uint64_t span = (uint64_t)(khi - klo + 1);
     if (span > dense_max) {  // sparse: every value looks up its own candidate block
       int64_t cb[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++)
-        cb[k] = valid[k] ? lane_ubound(f.first, klo, khi, v[k]) : klo - 1;
+      lane_ubound4(f.first, klo, khi, v, valid, cb);
       lookup_probes(f, v, valid, cb, klo, hit, lane, status);
       return;
     }
