@@ -8,8 +8,15 @@ Inputs (1.9 GB compressed) and outputs (8 GiB) are far larger than L2, so no
 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--layout gpu|paper|pfor] [--lists L] [--no-extra]
+                  [--queries-only --query-scale S]
 
-Prints one JSON line.  With N > 1 (torchrun) every rank decodes its own 32
+Prints one JSON line.  Besides the timed step it measures (unless
+--no-extra): decode+sum, clustered lists, the paper layout, the DM/D2/D1
+kinds, S4-FastPFOR, a per-bit-width unpack sweep with the two-pass prefix
+ablation, fused vs unfused pair intersections, 64 pairs per launch, batched
+conjunctive queries (with and without bitmaps), open-loop serving, the end
+to end call from host memory, and the oracle on the host cores.  With N > 1 (torchrun) every rank decodes its own 32
 lists (weak scaling, no collective on the data path); the reported value is
 all ranks' integers over the slowest rank's time.
 """

@@ -227,9 +227,9 @@ __device__ __forceinline__ uint32_t term_view(const uint8_t *data, const bp_list
 
 // Clears the bits of `alive` whose candidates (value 128g + 32j + lane of
 // s_r for bit 4g+j) are not set in the bitmap: one load per candidate.
-__device__ __noinline__ uint32_t bitmap_filter(const uint32_t *__restrict__ bm, uint32_t words,
-                                               const uint32_t *s_r, uint32_t ng, uint32_t alive,
-                                               int lane) {
+__device__ __forceinline__ uint32_t bitmap_filter(const uint32_t *__restrict__ bm,
+                                                  uint32_t words, const uint32_t *s_r, uint32_t ng,
+                                                  uint32_t alive, int lane) {
   for (uint32_t g = 0; g < ng; g++)
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -241,14 +241,14 @@ __device__ __noinline__ uint32_t bitmap_filter(const uint32_t *__restrict__ bm, 
   return alive;
 }
 
-// One work item of a query whose terms are all bitmaps.  Not inlined: it
-// keeps its registers out of the Set-vs-Set loop of q_main_kernel.
-__device__ __noinline__ void bitmap_and_item(const uint8_t *__restrict__ data,
-                                             const bp_list *__restrict__ lists, const TermView &V1,
-                                             const uint32_t *sorted, uint32_t k, uint32_t c,
-                                             uint32_t q, uint32_t item, QScratch sc,
-                                             uint64_t arena_cap, uint32_t *s_r, int lane,
-                                             uint32_t *status) {
+// One work item of a query whose terms are all bitmaps (only the hybrid
+// instance of q_main_kernel contains it).
+__device__ __forceinline__ void bitmap_and_item(const uint8_t *__restrict__ data,
+                                                const bp_list *__restrict__ lists,
+                                                const TermView &V1, const uint32_t *sorted,
+                                                uint32_t k, uint32_t c, uint32_t q, uint32_t item,
+                                                QScratch sc, uint64_t arena_cap, uint32_t *s_r,
+                                                int lane, uint32_t *status) {
   // Bitmaps sort last, so every term is a bitmap: AND kBitmapItemWords
   // words of all of them (lane l keeps words 32i + l in s_r), then write
   // the set bits of the result straight to the arena
