@@ -366,8 +366,8 @@ def unpack_sweep(stream, reps: int = 20, lists: int = 12, n: int = 1 << 20):
             for mode, fn in (("batch", lambda: batch.decode_into(out, status, stream)),
                              ("one_pass", lambda: batch.ablation_into(out, status, 0, stream)),
                              ("two_pass", lambda: batch.ablation_into(out, status, 1, stream))):
-                out.fill_(-1)
-                with torch.cuda.stream(stream):
+                with torch.cuda.stream(stream):  # the fill must land before the decode
+                    out.fill_(-1)
                     fn()
                 stream.synchronize()
                 assert int(status.item()) == 0 and torch.equal(out, want), (kname, b, mode)

@@ -240,6 +240,21 @@ def test_decode_ablation_any_width_and_order(orc, mode):
     assert np.array_equal(api.as_u32(batch.decode()), want)
 
 
+def test_decode_batch_kinds_short_output():
+    """A batch whose last list (DM) does not fit the output records
+    BP_ERR_CAPACITY; the lists that fit are decoded."""
+    xs = [W.uniform(5000 + 1000 * i, 0, 1 << 28, 7100 + i) for i in range(3)]
+    encs = [capi.bp_encode(x, capi.BP_LAYOUT_GPU, delta=k) for x, k in zip(xs, (0, 2, 1))]
+    batch = api.ListBatch(encs, [x.size for x in xs], capi.BP_LAYOUT_GPU)
+    short = xs[0].size + xs[1].size + 10
+    out = torch.full((short,), -1, dtype=torch.int32, device="cuda")
+    st = api.status_tensor()
+    batch.decode_into(out, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == capi.BP_ERR_CAPACITY
+    assert np.array_equal(api.as_u32(out[:short - 10]), np.concatenate(xs[:2]))
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_decode_batch_host(orc, layout):
     """bp_decode_batch_host from pinned host memory to pinned host memory.
