@@ -9,7 +9,7 @@ flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--layout gpu|paper|pfor] [--lists L] [--no-extra]
-                  [--queries-only --query-scale S]
+                  [--pairs-only] [--queries-only --query-scale S]
 
 Prints one JSON line.  Besides the timed step it measures (unless
 --no-extra): decode+sum, clustered lists, the paper layout, the DM/D2/D1
@@ -59,6 +59,8 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true", help="skip secondary measurements")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--pairs-only", action="store_true",
+                   help="run only the pair sweep (for profiling)")
     p.add_argument("--queries-only", action="store_true",
                    help="run only the batched-query measurement (for profiling)")
     p.add_argument("--query-scale", type=int, default=1,
@@ -986,6 +988,14 @@ def main():
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.pairs_only:
+        # the pair sweep alone (for profiling the pair kernels); one JSON line
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        stream = torch.cuda.Stream()
+        print(json.dumps({"pair_sweep": pair_sweep(stream, reps=args.steps)}), flush=True)
         return
     if args.queries_only:
         # the batched-query measurement alone, on an index `--query-scale`

@@ -34,8 +34,8 @@ struct PairArgs {
 constexpr int kPairGroups = 8;
 constexpr int kPairWarpWords = kPairGroups * 128 + kIxDenseMax * 128;
 
-// vpw: values of the shorter list per warp, a power of two: 8..128 (a slice
-// of one block, for very skewed pairs) or 128 g for g = 2..8 blocks, which
+// vpw: values of the shorter list per warp: a power of two 8..128 (a slice
+// of one block, for very skewed pairs) or 128 g for g = 1..8 blocks, which
 // the warp filters run by run with its window of f moving forward.
 __global__ void __launch_bounds__(kIxThreads)
     fused_pair_kernel(PairArgs a, Compaction cp, TileOut to, uint32_t ntiles, uint32_t dense_max,
@@ -148,9 +148,11 @@ uint32_t pair_tiles(uint64_t nr, uint32_t vpw = 128) {
 
 // Values of the shorter list per warp.  Very skewed pairs (every value
 // probes a block of its own, ratio >= 128) with too few values to fill the
-// GPU: down to 8 (more warps, fewer probes each).  Otherwise runs of up to 8
-// blocks per warp, as many as keep 16 warps per SM busy.
-uint32_t pair_vpw(uint64_t nr, uint64_t nf) {
+// GPU: down to 8 (more warps, fewer probes each).  Otherwise runs of g <= 8
+// blocks per warp: among the g that keep at least 16 warps per SM busy, the
+// one whose CTAs fill the `resident` CTA slots most evenly (the last wave
+// least empty; the larger g on a tie), else g = 1.
+uint32_t pair_vpw(uint64_t nr, uint64_t nf, uint64_t resident) {
   if (nr == 0) return 128;
   if (nf >= 128 * nr) {
     const uint64_t want_warps = 16ull * device_sm_count() * 8;
@@ -159,9 +161,20 @@ uint32_t pair_vpw(uint64_t nr, uint64_t nf) {
     return vpw;
   }
   const uint64_t want_warps = 16ull * device_sm_count();
-  uint32_t g = kPairGroups;
-  while (g > 1 && (nr + 128ull * g - 1) / (128ull * g) < want_warps) g >>= 1;
-  return 128u * g;
+  uint32_t best = 1;
+  double best_fill = -1.0;
+  for (uint32_t g = kPairGroups; g >= 1; g--) {
+    const uint64_t warps = (nr + 128ull * g - 1) / (128ull * g);
+    if (warps < want_warps) continue;
+    const uint64_t tiles = (warps + kIxWarps - 1) / kIxWarps;
+    const uint64_t waves = (tiles + resident - 1) / resident;
+    const double fill = (double)tiles / (double)(waves * resident);
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      best = g;
+    }
+  }
+  return 128u * best;
 }
 
 int g_pair_smem_set = 0;
@@ -195,14 +208,19 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
   TileOut to{out, out_cap, count, status};
   const Tuning &tu = tuning();
   if (mode == BP_MODE_FUSED) {
-    const uint32_t vpw = pair_vpw(a.nr, a.nf);
-    const uint32_t ft = pair_tiles(a.nr, vpw);
+    static int per_sm = 0;  // resident CTAs of fused_pair_kernel per SM
     if (!g_pair_smem_set) {
       if (cudaFuncSetAttribute(fused_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kPairSmem) != cudaSuccess)
         return BP_ERR_CUDA;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pair_kernel, kIxThreads,
+                                                        kPairSmem) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
       g_pair_smem_set = 1;
     }
+    const uint32_t vpw = pair_vpw(a.nr, a.nf, (uint64_t)per_sm * device_sm_count());
+    const uint32_t ft = pair_tiles(a.nr, vpw);
     if (cudaMemsetAsync(sp, 0, compaction_bytes(ft), s) != cudaSuccess) return BP_ERR_CUDA;
     fused_pair_kernel<<<ft, kIxThreads, kPairSmem, s>>>(
         a, cp, to, ft, std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw);
