@@ -301,7 +301,8 @@ size_t bp_intersect_scratch_bytes(size_t n_a, size_t n_b, int layout, int mode);
  * bp_decode (device, 16-byte aligned, n checked against the header).
  * Writes min(count, out_cap) values to d_out and the count to *d_count
  * (device uint32); count > out_cap records BP_ERR_CAPACITY (out_cap >=
- * min(n_a, n_b) always suffices).  mode: bp_mode; BP_MODE_FUSED needs
+ * min(n_a, n_b) always suffices).  layout: BP_LAYOUT_PAPER or
+ * BP_LAYOUT_GPU (BP_ERR_ARG otherwise); mode: bp_mode; BP_MODE_FUSED needs
  * BP_LAYOUT_GPU (else BP_ERR_ARG).  Scratch: bp_intersect_scratch_bytes;
  * the call enqueues a memset of part of it. */
 int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a,
