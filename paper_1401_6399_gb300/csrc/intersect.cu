@@ -12,6 +12,8 @@
 //      decoded arrays are intersected by the same warp-level regimes.
 // Output: ballot/popc inside warps, a CTA scan, and a decoupled look-back
 // across CTAs, so the result is written once, sorted, in a single pass.
+#include <mutex>
+
 #include "decode.h"
 #include "intersect.cuh"
 #include "tuning.h"
@@ -179,7 +181,11 @@ uint32_t pair_vpw(uint64_t nr, uint64_t nf, uint64_t resident) {
   return 128u * best;
 }
 
-int g_pair_smem_set = 0;
+// Per device (bit d: device d): the kernel's shared-memory limit was raised
+// and its resident CTAs per SM are in g_pair_per_sm[d].
+std::mutex g_pair_mu;
+uint64_t g_pair_smem_set = 0;
+int g_pair_per_sm[64];
 constexpr size_t kPairSmem = sizeof(uint32_t) * kPairWarpWords * kIxWarps;
 
 }  // namespace
@@ -210,16 +216,23 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
   TileOut to{out, out_cap, count, status};
   const Tuning &tu = tuning();
   if (mode == BP_MODE_FUSED) {
-    static int per_sm = 0;  // resident CTAs of fused_pair_kernel per SM
-    if (!g_pair_smem_set) {
-      if (cudaFuncSetAttribute(fused_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kPairSmem) != cudaSuccess)
-        return BP_ERR_CUDA;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pair_kernel, kIxThreads,
-                                                        kPairSmem) != cudaSuccess ||
-          per_sm < 1)
-        per_sm = 1;
-      g_pair_smem_set = 1;
+    int dev = 0, per_sm = 1;  // resident CTAs of fused_pair_kernel per SM
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BP_ERR_CUDA;
+    {
+      std::lock_guard<std::mutex> g(g_pair_mu);
+      if (!((g_pair_smem_set >> dev) & 1u)) {
+        if (cudaFuncSetAttribute(fused_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kPairSmem) != cudaSuccess)
+          return BP_ERR_CUDA;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_pair_kernel, kIxThreads,
+                                                          kPairSmem) != cudaSuccess ||
+            n < 1)
+          n = 1;
+        g_pair_per_sm[dev] = n;
+        g_pair_smem_set |= 1ull << dev;
+      }
+      per_sm = g_pair_per_sm[dev];
     }
     const uint32_t vpw = pair_vpw(a.nr, a.nf, (uint64_t)per_sm * device_sm_count());
     const uint32_t ft = pair_tiles(a.nr, vpw);

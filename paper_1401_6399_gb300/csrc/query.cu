@@ -20,6 +20,7 @@
 // bp_query_one (one query, plain): decode every list of the query to
 // scratch, then intersect the decoded arrays two at a time from the
 // shortest (the paper's decompress-then-intersect SvS of Section 7.6).
+#include <mutex>
 #include <vector>
 
 #include "decode.h"
@@ -527,7 +528,10 @@ __global__ void q_gather_kernel(QScratch sc, uint32_t nq, uint32_t max_items,
 
 __global__ void set_u32_kernel(uint32_t *p, uint32_t v) { *p = v; }
 
-int g_main_smem_set = 0;
+// Devices (bit d: device d) on which q_main_kernel's shared-memory limit
+// was raised.
+std::mutex g_main_mu;
+uint64_t g_main_smem_set = 0;
 
 }  // namespace
 
@@ -580,13 +584,18 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
   if (nq == 0) return BP_OK;
   const int threads = 32 * (int)warps;
   const size_t smem = sizeof(uint32_t) * kWarpSmemWords * warps;
-  if (!g_main_smem_set) {
-    if (cudaFuncSetAttribute(q_main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess ||
-        cudaFuncSetAttribute(q_main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess)
-      return BP_ERR_CUDA;
-    g_main_smem_set = 1;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BP_ERR_CUDA;
+    std::lock_guard<std::mutex> g(g_main_mu);
+    if (!((g_main_smem_set >> dev) & 1u)) {
+      if (cudaFuncSetAttribute(q_main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess ||
+          cudaFuncSetAttribute(q_main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess)
+        return BP_ERR_CUDA;
+      g_main_smem_set |= 1ull << dev;
+    }
   }
   int per_sm = 0, per_sm_h = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_main_kernel<false>, threads,
