@@ -113,6 +113,29 @@ def test_pfor_encoder_matches_oracle_bytes(orc):
             assert e.size <= capi.bp_encode_bound(n, capi.BP_LAYOUT_PFOR)
 
 
+def test_pfor_stream_info_rejects_bad_headers_and_bound_holds():
+    """The host header parser rejects GP headers whose geometry, length or
+    kind do not add up; the encoder never exceeds bp_encode_bound, also for
+    blocks of width 32 and blocks full of exceptions."""
+    rng = np.random.default_rng(63)
+    for x in (rng.integers(0, 1 << 32, 9000, dtype=np.uint64).astype(np.uint32),
+              W.stepped_walk(4096 * 3 + 1, 32, 64), W.stepped_walk(777, 0, 65)):
+        for kind in range(4):
+            e = capi.bp_encode(x, capi.BP_LAYOUT_PFOR, 2, kind | capi.BP_ENCODE_ANY_ORDER)
+            assert e.size <= capi.bp_encode_bound(x.size, capi.BP_LAYOUT_PFOR)
+    x = np.arange(5, 5 + 3 * 20000, 3, dtype=np.uint32)
+    e = capi.bp_encode(x, capi.BP_LAYOUT_PFOR, 1)
+    assert capi.bp_stream_info(e) == (x.size, capi.BP_LAYOUT_PFOR)
+    for word, value in ((0, 0x12345678), (3, 7), (4, 99), (8, 12), (12, 4)):
+        bad = e.copy()
+        bad[4 * word:4 * word + 4] = np.array([value], np.uint32).view(np.uint8)
+        with pytest.raises(capi.BPError) as err:
+            capi.bp_stream_info(bad)
+        assert err.value.code == capi.BP_ERR_CORRUPT
+    with pytest.raises(capi.BPError):
+        capi.bp_stream_info(e[:-4])  # shorter than the header's total
+
+
 def test_hybrid_index_bitmaps():
     """hyb+m2 index: a list whose average gap is at most B becomes a bitmap
     (bit v set iff v is in the list; header {magic, 2, n, words}), the others
