@@ -65,6 +65,11 @@ def parse_args():
                    help="run only the batched-query measurement (for profiling)")
     p.add_argument("--query-scale", type=int, default=1,
                    help="with --queries-only: index and batch this many times smaller")
+    p.add_argument("--serving-sweep", action="store_true",
+                   help="only the serving engine at 1M queries/s offered over slot counts "
+                        "and batch sizes")
+    p.add_argument("--profile-case", choices=["decode_sum", "gp_decode", "pl_decode"],
+                   help="time one small decode case alone (for ncu): 4 lists of 2^26")
     return p.parse_args()
 
 
@@ -243,45 +248,84 @@ def oracle_decode_rate(encs, ns, threads: int, layout: int = 1):
     dec = {0: orc.pl_decode, 1: orc.gl_decode, 3: orc.gp_decode}[layout]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        outs = list(ex.map(lambda e: dec(e.tobytes()), encs))
+        outs = list(ex.map(dec, encs))
     dt = time.perf_counter() - t0
     assert [o.size for o in outs] == list(ns)
     return sum(ns) / dt / 1e9, dt, threads
 
 
+def oracle_query_rates(data, h_lists, terms, toff, qids, threads: int):
+    """The oracle answering queries from the compressed index, as a CPU
+    system would: every term's GL stream decoded by the scalar oracle, then
+    Set-vs-Set by merging (orc.svs).  Each query runs on one thread, queries
+    spread over `threads` threads (closed loop).  Returns (queries/s, per-
+    query service times in s, answer counts)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import Oracle
+    orc = Oracle()
+    eo = h_lists["enc_offset"].astype(np.int64)
+    eb = h_lists["enc_bytes"].astype(np.int64)
+
+    def one(q):
+        t0 = time.perf_counter()
+        t = terms[int(toff[q]):int(toff[q + 1])]
+        lists = [orc.gl_decode(data[eo[u]:eo[u] + eb[u]]) for u in t]
+        k = orc.svs(lists).size
+        return time.perf_counter() - t0, k
+
+    w0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        res = list(ex.map(one, [int(q) for q in qids]))
+    wall = time.perf_counter() - w0
+    return len(qids) / wall, np.array([r[0] for r in res]), np.array([r[1] for r in res])
+
+
 def run_reference(args, rank, world):
-    """Reference arm: the oracle (scalar C) on the host cores; each step
-    decodes a bounded sample of the workload: 16 lists of 2^22 integers of
-    the same distribution (uniform, density 1/8, [0, 2^25))."""
+    """Reference arm: the scalar C oracle on the host cores, on the headline
+    decode workload itself: 32 lists of 2^26 uniform integers of [0, 2^29)
+    in the GPU layout, written by the oracle's own encoder; every step
+    decodes all of them, lists spread over the host threads."""
     if rank != 0:
         return
-    from oracle import build_oracle
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import Oracle, build_oracle
     from workloads.workloads import build_workloads
-    from paper_1401_6399_gb300.build import build
-    build()
     build_oracle()
     build_workloads()
-    from paper_1401_6399_gb300 import capi
+    orc = Oracle()
     threads = min(16, os.cpu_count() or 1)
-    n = 1 << 22
-    lists = make_lists("uniform", threads, n, 1 << 25, SEED_BASE)
-    encs = [capi.bp_encode(x, capi.BP_LAYOUT_GPU, nthreads=4) for x in lists]
+    n = 1 << args.log2n
+    L = args.lists
+    lists = make_lists("uniform", L, n, UNIVERSE, SEED_BASE)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        encs = list(ex.map(lambda x: np.frombuffer(orc.gl_encode(x), np.uint8), lists))
+    assert np.array_equal(orc.gl_decode(encs[0]), lists[0])
+    del lists
+    comp = sum(e.size for e in encs)
+
+    def step():
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            outs = list(ex.map(lambda e: orc.gl_decode(e).size, encs))
+        assert outs == [n] * L
+
     for _ in range(args.warmup):
-        oracle_decode_rate(encs, [n] * threads, threads)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_decode_rate(encs, [n] * threads, threads)
+        step()
     dt = time.perf_counter() - t0
-    ints = n * threads * args.steps
-    val = ints / dt / 1e9
-    sample = f"{threads} lists x 2^22 uniform ints of [0,2^25) per step, GL streams, scalar oracle"
+    val = n * L * args.steps / dt / 1e9
+    sample = (f"the whole workload every step: {L} GL streams of 2^{args.log2n} ints "
+              f"(oracle-encoded, {comp} bytes) decoded by the scalar C oracle on {threads} threads")
     line = {"metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "decode 32 lists x 2^26 uniform uint32 of [0,2^29), S4-BP128-D4 "
-                                   "GPU layout (bounded CPU sample per step)",
-                       "l2": "inputs larger than L2"},
+            "config": {"workload": f"decode {L} lists x 2^{args.log2n} uniform uint32 of "
+                                   "[0,2^29) per GPU, S4-BP128-D4 GPU layout",
+                       "lists_per_gpu": L, "ints_per_list": n, "compressed_bytes_per_gpu": comp,
+                       "l2": "inputs (compressed) and outputs larger than L2; no flush"},
             "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": threads,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -384,10 +428,12 @@ def unpack_sweep(stream, reps: int = 20, lists: int = 12, n: int = 1 << 20):
     return {"widths": "0..32", "ints_per_launch": total, "gints": res}
 
 
-def pair_sweep(stream, reps: int):
+def pair_sweep(stream, reps: int, cpu_threads: int = 0):
     """Longer list 2^22 uniform values of [0,2^26); shorter lists of 2^22 .. 2^8
     values sharing 10% of theirs; fused vs unfused bp_intersect_pair, L2
-    flushed before every call (one pair fits in L2)."""
+    flushed before every call (one pair fits in L2).  cpu_threads > 0: the
+    oracle beside it (decode both streams, merge), one pair on one thread and
+    one pair per thread on cpu_threads threads."""
     import torch
     import workloads as W
     from paper_1401_6399_gb300 import api, capi
@@ -444,8 +490,33 @@ def pair_sweep(stream, reps: int):
         row["fused_alg_bytes"] = alg
         row["fused_gbs"] = round(alg / (row["fused_us"] * 1e-6) / 1e9, 1)
         row["candidate_blocks"] = int(cand.size)
+        if cpu_threads:
+            row.update(cpu_pair_rates(encr, encf, k, cpu_threads))
+            row["gpu_vs_cpu_1t"] = round(row["cpu_us_1t"] / row["fused_us"], 1)
         out[f"m=2^{int(np.log2(m))}"] = row
     return out
+
+
+def cpu_pair_rates(encr, encf, k: int, threads: int) -> dict:
+    """The oracle on one pair of GL streams: decode both, intersect by merge
+    (Section 6), on one thread (best of 3) and as `threads` concurrent pairs."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import Oracle
+    orc = Oracle()
+
+    def pair():
+        return orc.intersect(orc.gl_decode(encr), orc.gl_decode(encf)).size
+    best = float("inf")
+    for _ in range(3):
+        t0 = time.perf_counter()
+        assert pair() == k
+        best = min(best, time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        assert list(ex.map(lambda _: pair(), range(threads))) == [k] * threads
+    wall = time.perf_counter() - t0
+    return {"cpu_us_1t": round(1e6 * best, 1), "cpu_pairs_per_s": round(threads / wall, 1),
+            "cpu_threads": threads}
 
 
 def pair_batch(stream, reps: int, pairs: int = 64):
@@ -579,7 +650,7 @@ def query_alg_bytes(idx, vals, offs, terms, toff, sample: int, seed: int) -> flo
 
 
 def batched_queries(stream, reps: int, plain_queries: int, scale: int = 1,
-                    hybrid_bs=(8, 16, 32)):
+                    hybrid_bs=(8, 16, 32), cpu_threads: int = 0):
     """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
     2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
     100,000 queries of 2-5 terms drawn in proportion to list length.  One
@@ -668,7 +739,22 @@ def batched_queries(stream, reps: int, plain_queries: int, scale: int = 1,
     peak, peak_kind = load_peaks()
     alg_gbs = apq * nq / (ms * 1e-3) / 1e9
     batched_queries.index = (idx, lens)  # reused by the serving measurement
-    return {"queries": nq, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
+    cpu = None
+    if cpu_threads:
+        # the oracle on the first queries of the batch: decode every term's
+        # stream, merge (Set-vs-Set); answer sizes must match the GPU's
+        qids = np.arange(min(800, nq))
+        qps_c, svc, kc = oracle_query_rates(idx.host_data, idx.h_lists, terms, toff, qids,
+                                            cpu_threads)
+        assert np.array_equal(kc, c[qids].astype(np.int64))
+        qps_1, _, _ = oracle_query_rates(idx.host_data, idx.h_lists, terms, toff, qids[:100], 1)
+        cpu = {"value": round(qps_c, 1), "unit": "queries/s", "cores": cpu_threads,
+               "kind": "oracle", "value_single_thread": round(qps_1, 1),
+               "sample": f"the first {qids.size} queries of the batch ({cpu_threads} threads; "
+                         "100 on one thread): every term's GL stream decoded by the scalar "
+                         "oracle, then Set-vs-Set by merging",
+               "gpu_vs_cpu": round(qps / qps_c, 1)}
+    return {"queries": nq, "cpu_baseline": cpu, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
             "plain_queries_timed": qn, "plain_queries_per_s": round(qps_plain, 1),
             "speedup_vs_plain": round(qps / qps_plain, 1), "answer_values": total,
             "index_postings": int(lens.sum()), "index_bytes": idx.compressed_bytes,
@@ -679,44 +765,135 @@ def batched_queries(stream, reps: int, plain_queries: int, scale: int = 1,
             "hbm_peak": f"{peak} GB/s ({peak_kind})", "hybrid": hybrid}
 
 
+def serving_warmup(srv, lens):
+    """An unmeasured replay that launches every kernel the engine uses, so
+    that module loading and first-launch set-up stay out of the runs."""
+    import workloads as W
+    wt, wo = W.queries(lens, 4000, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x50FF)
+    srv.replay(np.arange(4000, dtype=np.uint64), wt, wo, W.poisson_arrivals(2e4, 4000, 0x51FF))
+    srv.drain(600.0)
+    srv.poll(with_answers=False)
+    srv.batches()
+
+
+def timeline_summary(recs, res) -> dict:
+    """Where the time of the slowest queries went, from the engine's batch
+    records: for the batch that held the slowest query, its wait before
+    admission, enqueue time and device time; and the largest of each over
+    all batches."""
+    if recs.size == 0:
+        return {}
+    lat = np.array([r[5] - r[3] for r in res])
+    worst = res[int(np.argmax(lat))]
+    # the batch that finished at the worst query's completion time
+    k = int(np.argmin(np.abs(recs["done_s"] - worst[5])))
+    b = recs[k]
+    gap = np.diff(np.sort(recs["done_s"]))
+
+    def ms(x):
+        return round(1e3 * float(x), 3)
+    return {"batches": int(recs.size),
+            "mean_queries_per_batch": round(float(recs["queries"].mean()), 1),
+            "worst_query_ms": ms(lat.max()),
+            "worst_batch": {"queries": int(b["queries"]), "slot": int(b["slot"]),
+                            "wait_before_admit_ms": ms(b["admit_s"] - b["first_arrival_s"]),
+                            "enqueue_ms": ms(b["launched_s"] - b["admit_s"]),
+                            "device_ms": ms(b["done_s"] - b["launched_s"])},
+            "max_wait_before_admit_ms": ms((recs["admit_s"] - recs["first_arrival_s"]).max()),
+            "max_enqueue_ms": ms((recs["launched_s"] - recs["admit_s"]).max()),
+            "max_device_ms": ms((recs["done_s"] - recs["launched_s"]).max()),
+            "max_gap_between_completions_ms": ms(gap.max()) if gap.size else 0.0}
+
+
+def serve_rate(srv, lens, rate: float, n: int, seed: int) -> dict:
+    """One open-loop run of n Poisson arrivals at `rate` queries/s.  Latency
+    = completion - scheduled arrival; lag = queued - scheduled arrival."""
+    import workloads as W
+    terms, toff = W.queries(lens, n, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, seed)
+    arrivals = W.poisson_arrivals(rate, n, seed + 0x100)
+    srv.batches()  # drop earlier records
+    srv.replay(np.arange(n, dtype=np.uint64), terms, toff, arrivals)
+    srv.drain(900.0)
+    res = srv.poll(with_answers=False)
+    recs = srv.batches()
+    assert len(res) == n and all(r[2] == 0 for r in res)
+    arr = np.array([r[3] for r in res])
+    sub = np.array([r[4] for r in res])
+    done = np.array([r[5] for r in res])
+    lat_ms = (done - arr) * 1e3
+    lag_ms = (sub - arr) * 1e3
+    span = done.max() - arr.min()
+    return {"queries": n, "offered_qps": rate, "offered_s": round(float(arrivals[-1]), 2),
+            "achieved_qps": round(n / span, 1),
+            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+            "p999_ms": round(float(np.percentile(lat_ms, 99.9)), 3),
+            "submit_lag_p99_ms": round(float(np.percentile(lag_ms, 99)), 4),
+            "submit_lag_max_ms": round(float(lag_ms.max()), 4),
+            "answer_values": int(sum(r[1] for r in res)),
+            "timeline": timeline_summary(recs, res)}
+
+
+def serving_cpu(idx, lens, threads: int, n: int = 1600) -> dict:
+    """The oracle as a closed-loop server on the serving mix (2-8 terms):
+    `threads` workers each take the next query when done with the last, so
+    a query's latency is its service time (decode every term's stream,
+    merge)."""
+    import workloads as W
+    terms, toff = W.queries(lens, n, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5000 + 100_000)
+    qps, svc, _ = oracle_query_rates(idx.host_data, idx.h_lists, terms, toff, np.arange(n),
+                                     threads)
+    ms = svc * 1e3
+    return {"value": round(qps, 1), "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "p50_ms": round(float(np.percentile(ms, 50)), 3),
+            "p99_ms": round(float(np.percentile(ms, 99)), 3),
+            "sample": f"{n} queries of the 2-8-term serving mix, closed loop on {threads} "
+                      "threads (latency = service time: decode every term, merge)"}
+
+
 def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
     """Open-loop Poisson arrivals of 2-8-term queries against the resident
     index; the engine batches continuously over 4 slots of 1 GiB (at most
-    4 GiB of scratch and answers in flight).  Latency = completion - arrival."""
-    import workloads as W
+    4 GiB of scratch and answers in flight).  Each rate runs for 10 s of
+    arrivals or 1e6 queries, whichever is fewer.  Latency = completion -
+    scheduled arrival."""
     from paper_1401_6399_gb300 import api
     out = {}
     srv = api.Server(idx, slots=4, max_batch_queries=8192, max_terms=8, slot_bytes=1 << 30,
                      deliver_answers=False)
     try:
-        # warm-up replay (not measured): lazy setup of the engine's streams
-        wt, wo = W.queries(lens, 2000, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x50FF)
-        srv.replay(np.arange(2000, dtype=np.uint64), wt, wo, W.poisson_arrivals(1e4, 2000, 0x51FF))
-        srv.drain(600.0)
-        srv.poll(with_answers=False)
+        serving_warmup(srv, lens)
         for rate in rates:
-            n = int(min(300_000, rate * 5))
-            terms, toff = W.queries(lens, n, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5000 + int(rate))
-            arrivals = W.poisson_arrivals(rate, n, 0x5100 + int(rate))
-            tags = np.arange(n, dtype=np.uint64)
-            srv.replay(tags, terms, toff, arrivals)
-            srv.drain(600.0)
-            res = srv.poll(with_answers=False)
-            assert len(res) == n and all(r[2] == 0 for r in res)
-            sub = np.array([r[3] for r in res])
-            done = np.array([r[4] for r in res])
-            lat_ms = (done - sub) * 1e3
-            span = done.max() - sub.min()
-            out[f"{int(rate)}/s"] = {
-                "queries": n, "offered_qps": rate, "achieved_qps": round(n / span, 1),
-                "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
-                "p999_ms": round(float(np.percentile(lat_ms, 99.9)), 3),
-                "answer_values": int(sum(r[1] for r in res))}
+            n = int(min(1_000_000, 10 * rate))
+            out[f"{int(rate)}/s"] = serve_rate(srv, lens, rate, n, 0x5000 + int(rate))
         out["engine"] = srv.stats()
     finally:
         srv.close()
     return out
+
+
+def serving_sweep(idx, lens, rate=1e6, n=1_000_000):
+    """Saturation of the engine at `rate` offered queries/s for several slot
+    counts and batch sizes, with 4 GiB in flight in total: is the achieved
+    rate set by the slots or by the device?"""
+    from paper_1401_6399_gb300 import api
+    rows = []
+    for slots in (2, 4, 8, 16):
+        for mbq in (1024, 8192, 65536):
+            srv = api.Server(idx, slots=slots, max_batch_queries=mbq, max_terms=8,
+                             slot_bytes=(4 << 30) // slots, deliver_answers=False)
+            try:
+                serving_warmup(srv, lens)
+                r = serve_rate(srv, lens, rate, n, 0x5000 + int(rate))
+                st = srv.stats()
+            finally:
+                srv.close()
+            rows.append({"slots": slots, "max_batch_queries": mbq,
+                         "achieved_qps": r["achieved_qps"], "p50_ms": r["p50_ms"],
+                         "p99_ms": r["p99_ms"], "max_busy_slots": st["max_busy_slots"],
+                         "mean_queries_per_batch": r["timeline"].get("mean_queries_per_batch"),
+                         "max_device_ms": r["timeline"].get("max_device_ms")})
+    return rows
 
 
 def run_ours(args, rank, world, local):
@@ -911,8 +1088,9 @@ def run_ours(args, rank, world, local):
             extra["unpack_sweep"] = unpack_sweep(stream)
         except Exception as e:
             extra["unpack_sweep"] = {"error": repr(e)[:300]}
+        cpu_t = 0 if (args.no_cpu or world > 1 or rank != 0) else min(16, os.cpu_count() or 1)
         try:
-            extra["pair_sweep"] = pair_sweep(stream, reps=20)
+            extra["pair_sweep"] = pair_sweep(stream, reps=20, cpu_threads=cpu_t)
         except Exception as e:  # report, do not hide the headline
             extra["pair_sweep"] = {"error": repr(e)[:300]}
         try:
@@ -921,12 +1099,15 @@ def run_ours(args, rank, world, local):
             extra["pair_batch_64"] = {"error": repr(e)[:300]}
         torch.cuda.empty_cache()
         try:
-            extra["batched_queries"] = batched_queries(stream, reps=5, plain_queries=2000)
+            extra["batched_queries"] = batched_queries(stream, reps=5, plain_queries=2000,
+                                                       cpu_threads=cpu_t)
         except Exception as e:
             extra["batched_queries"] = {"error": repr(e)[:300]}
         try:
             if hasattr(batched_queries, "index"):
                 extra["serving"] = serving(*batched_queries.index)
+                if cpu_t:
+                    extra["serving"]["cpu_baseline"] = serving_cpu(*batched_queries.index, cpu_t)
                 del batched_queries.index
         except Exception as e:
             extra["serving"] = {"error": repr(e)[:300]}
@@ -983,6 +1164,34 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def profile_case(args) -> dict:
+    """A small case of one decode kernel, launched warmup + steps times on
+    its own (the command ncu captures): 4 lists of 2^26 uniform integers,
+    more than L2 in and out."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1401_6399_gb300 import api, capi
+    n, L = 1 << args.log2n, 4
+    lists = make_lists("uniform", L, n, UNIVERSE, SEED_BASE)
+    layout = {"decode_sum": capi.BP_LAYOUT_GPU, "gp_decode": capi.BP_LAYOUT_PFOR,
+              "pl_decode": capi.BP_LAYOUT_PAPER}[args.profile_case]
+    batch = api.ListBatch(encode_all(lists, layout), [n] * L, layout)
+    stream = torch.cuda.Stream()
+    status = api.status_tensor()
+    if args.profile_case == "decode_sum":
+        sums = torch.zeros(L, dtype=torch.int64, device="cuda")
+        fn = lambda: batch.sum_into(sums, status, stream)  # noqa: E731
+    else:
+        out = torch.empty(n * L, dtype=torch.int32, device="cuda")
+        fn = lambda: batch.decode_into(out, status, stream)  # noqa: E731
+    ms = time_launches(stream, fn, args.steps, args.warmup)
+    assert int(status.item()) == 0
+    return {"profile_case": args.profile_case, "lists": L, "ints_per_list": n,
+            "ms": round(ms, 4), "gints": round(n * L / (ms * 1e-3) / 1e9, 2),
+            "compressed_bytes": batch.compressed_bytes}
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_setup(args)
@@ -996,6 +1205,18 @@ def main():
         ge.build()
         stream = torch.cuda.Stream()
         print(json.dumps({"pair_sweep": pair_sweep(stream, reps=args.steps)}), flush=True)
+        return
+    if args.serving_sweep:
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        stream = torch.cuda.Stream()
+        batched_queries(stream, reps=2, plain_queries=10, hybrid_bs=())
+        idx, lens = batched_queries.index
+        print(json.dumps({"serving_sweep": serving_sweep(idx, lens)}), flush=True)
+        return
+    if args.profile_case:
+        print(json.dumps(profile_case(args)), flush=True)
         return
     if args.queries_only:
         # the batched-query measurement alone, on an index `--query-scale`

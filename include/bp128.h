@@ -140,12 +140,24 @@ typedef enum {
  * blocks that some value falls in, found by binary search over the skip
  * headers (skewed lengths, the galloping regime).  query_chunk_blocks is the
  * number of blocks of a query's shortest list per work item in
- * bp_query_batch, query_warps the warps per CTA of its persistent kernel. */
+ * bp_query_batch, query_warps the warps per CTA of its persistent kernel.
+ *
+ * The last two fields bound and test the waits of the ordered output of
+ * bp_intersect_pair (each CTA, in ticket order, waits for the output counts
+ * of the CTAs before it).  lookback_spin_limit is the number of polls of
+ * one predecessor's count before the wait gives up, records BP_ERR_TIMEOUT
+ * in the status word and carries on (0: the default, 2^22 polls, seconds).
+ * withhold_tile = k > 0 makes tile k - 1 of every later pair call publish
+ * no count, so that the tiles after it exhaust their polls: it exists to
+ * show that such a wait ends and is reported, and must stay 0 otherwise
+ * (the output of a call made with it is wrong by design). */
 typedef struct bp_tuning {
-  uint32_t dense_blocks;       /* 1..8, default 4 */
-  uint32_t query_chunk_blocks; /* 1..8, default 1 */
-  uint32_t query_warps;        /* 4 or 8, default 8 */
-  uint32_t reserved[5];
+  uint32_t dense_blocks;        /* 1..8, default 4 */
+  uint32_t query_chunk_blocks;  /* 1..8, default 1 */
+  uint32_t query_warps;         /* 4 or 8, default 8 */
+  uint32_t lookback_spin_limit; /* 0 (default 2^22) or 1..2^22 */
+  uint32_t withhold_tile;       /* 0 (none), or 1 + the tile to withhold */
+  uint32_t reserved[3];
 } bp_tuning;
 
 /* Status text for a bp_status code (static string, never NULL). */
@@ -316,17 +328,22 @@ int bp_intersect_pair(const uint8_t *d_a, size_t a_bytes, size_t n_a,
  * a plug-in that only works on the buffers its host framework hands it, a
  * server whose pool already holds all device memory, or latency-bound code
  * that must not call cudaMalloc (it can synchronise the device) has no way
- * to provide the scratch buffer bp_intersect_pair asks for.  This call does the
- * same fused intersection of two BP_LAYOUT_GPU lists (arguments, output and
- * errors as in bp_intersect_pair with BP_MODE_FUSED) but keeps its scratch
- * in a 256 KiB array of device memory that the library reserves on every GPU
- * that loads it, for the life of the process; it allocates nothing.  The
- * shorter list may hold at most BP_NOALLOC_MAX_SHORT_LIST integers (larger:
- * BP_ERR_SCRATCH, nothing enqueued).  The first call on a device looks up
- * the array's device address (a runtime call), so make that first call
- * before any stream capture.  All calls share the array and each clears the
- * part it uses: calls whose work overlaps on the GPU corrupt each other's
- * results, so issue them in order on one stream. */
+ * to provide the scratch buffer bp_intersect_pair asks for.  This call
+ * computes the same intersection of two BP_LAYOUT_GPU lists (arguments,
+ * output and errors as in bp_intersect_pair with BP_MODE_FUSED) with a
+ * simpler, fixed schedule -- one block of 128 values of the shorter list
+ * per warp, no choice of run length, no shared-memory window carried from
+ * run to run -- so its speed can differ from bp_intersect_pair's, most on
+ * very skewed pairs.  It keeps its scratch in a 256 KiB array of device
+ * memory that the library reserves on every GPU that loads it, for the life
+ * of the process; it allocates nothing.  The shorter list may hold at most
+ * BP_NOALLOC_MAX_SHORT_LIST integers (larger: BP_ERR_SCRATCH, nothing
+ * enqueued).  The first call on a device looks up the array's device
+ * address (a runtime call) and keeps it, so make that first call before any
+ * stream capture, and do not use the call again on a device after
+ * cudaDeviceReset (the kept address would be stale).  All calls share the
+ * array and each clears the part it uses: calls whose work overlaps on the
+ * GPU corrupt each other's results, so issue them in order on one stream. */
 #define BP_NOALLOC_MAX_SHORT_LIST 33552384u
 int bp_intersect_pair_noalloc(const uint8_t *d_a, size_t a_bytes, size_t n_a,
                               const uint8_t *d_b, size_t b_bytes, size_t n_b,
@@ -408,13 +425,28 @@ typedef struct bp_server_config {
   uint64_t reserved[4];
 } bp_server_config;
 
+/* Times are steady-clock seconds.  arrival_s is when the query was due:
+ * its scheduled arrival under bp_server_replay, else the moment
+ * bp_server_submit was called; submit_s is when it entered the queue
+ * (submit_s - arrival_s is the load generator's lag); done_s is when the
+ * dispatcher saw its batch finish.  Latency = done_s - arrival_s. */
 typedef struct bp_server_result {
   uint64_t tag;
   uint32_t count;          /* answer values                               */
   int32_t status;          /* BP_OK, or the error of the query's batch    */
-  double submit_s, done_s; /* steady-clock seconds: submission, completion */
+  double arrival_s, submit_s, done_s;
   const uint32_t *answer;  /* deliver_answers = 1: valid until the next poll */
 } bp_server_result;
+
+/* One launched batch, for a timeline of the engine: the slot, its queries,
+ * the earliest arrival among them, when admission started, when the
+ * launches had been enqueued, when the dispatcher saw the batch finish,
+ * and when its answers were handed over. */
+typedef struct bp_server_batch {
+  uint32_t slot, queries;
+  uint64_t answer_values;
+  double first_arrival_s, admit_s, launched_s, done_s, retired_s;
+} bp_server_batch;
 
 /* Device bytes (slots x slot_bytes) and pinned host bytes the engine needs. */
 size_t bp_server_device_bytes(const bp_server_config *cfg);
@@ -434,7 +466,8 @@ int bp_server_submit(bp_server *s, uint64_t tag, const uint32_t *terms,
 
 /* Open-loop load: submit query i (terms[term_off[i]..term_off[i+1])) at
  * arrival_s[i] seconds after the call starts, on the calling thread,
- * whatever the engine's progress. */
+ * whatever the engine's progress.  Each query's arrival_s in its result is
+ * that scheduled time, so a late submission counts in its latency. */
 int bp_server_replay(bp_server *s, const uint64_t *tags, const uint32_t *terms,
                      const uint64_t *term_off, uint32_t n,
                      const double *arrival_s);
@@ -449,6 +482,10 @@ int bp_server_drain(bp_server *s, double timeout_s);
 /* out = {submitted, completed, batches launched, rejected (too large for a
  * slot), most slots busy at once, queries waiting}. */
 int bp_server_stats(bp_server *s, uint64_t out[6]);
+
+/* Move up to max records of retired batches (oldest first) to out; returns
+ * how many.  The engine keeps the records of the last 2^20 batches. */
+uint32_t bp_server_batches(bp_server *s, bp_server_batch *out, uint32_t max);
 
 /* Finish the queued and running queries, then stop the engine. */
 void bp_server_destroy(bp_server *s);

@@ -193,16 +193,22 @@ class Oracle:
             raise OracleError(rc, fn.__name__)
         return out[: nbytes.value].tobytes()
 
-    def _decode(self, fn, data: bytes) -> np.ndarray:
-        buf = np.frombuffer(bytes(data), np.uint8)
-        buf = buf.copy() if buf.size else np.zeros(1, np.uint8)
+    def _decode(self, fn, data) -> np.ndarray:
+        """data: bytes, or a C-contiguous uint8 array (read in place)."""
+        if (isinstance(data, np.ndarray) and data.dtype == np.uint8
+                and data.flags.c_contiguous and data.size):
+            buf, nbytes = data, data.size
+        else:
+            buf = np.frombuffer(bytes(data), np.uint8)
+            nbytes = buf.size
+            buf = buf.copy() if buf.size else np.zeros(1, np.uint8)
         n = _sz(0)
-        rc = self.lib.orc_stream_count(buf, len(data), C.byref(n))
+        rc = self.lib.orc_stream_count(buf, nbytes, C.byref(n))
         if rc:
             raise OracleError(rc, "stream_count")
-        out = np.zeros(max(1, n.value), np.uint32)
+        out = np.empty(max(1, n.value), np.uint32)
         got = _sz(0)
-        rc = fn(buf, len(data), out, out.size, C.byref(got))
+        rc = fn(buf, nbytes, out, out.size, C.byref(got))
         if rc:
             raise OracleError(rc, fn.__name__)
         return out[: got.value]
@@ -292,3 +298,21 @@ class Oracle:
         out = np.zeros(max(1, min([len(x) for x in lists] or [0])), np.uint32)
         k = self.lib.orc_svs(ptrs, lens, len(lists), out)
         return out[:k]
+
+    def svs_gallop(self, lists) -> np.ndarray:
+        """Set-vs-Set (Section 6) with every step done by galloping: the
+        lists in increasing order of length (ties in the given order), the
+        candidates start as the shortest list and are intersected with each
+        longer list in turn by orc_intersect_gallop; stops once no candidate
+        is left.  Same result as svs (the intersection is unique); the cost
+        is O(m log n) per step instead of O(m + n), which makes sets with
+        lists of 2^24 values affordable."""
+        if not len(lists):
+            return np.zeros(0, np.uint32)
+        order = sorted(range(len(lists)), key=lambda i: len(lists[i]))
+        cur = _u32(lists[order[0]])
+        for i in order[1:]:
+            if cur.size == 0:
+                break
+            cur = self.intersect_gallop(cur, lists[i])
+        return cur.copy() if cur.base is not None else cur

@@ -292,6 +292,8 @@ class Server:
                                         arrival_s.ctypes.data), "bp_server_replay")
 
     def poll(self, with_answers: bool = True) -> list:
+        """Finished queries as (tag, count, status, arrival_s, submit_s,
+        done_s, answer) tuples; latency is done_s - arrival_s."""
         out = []
         while True:
             n = capi.lib.bp_server_poll(self.ptr, self._res, len(self._res))
@@ -302,10 +304,26 @@ class Server:
                     ans = np.ctypeslib.as_array(r.answer, shape=(r.count,)).copy()
                 elif with_answers and r.status == capi.BP_OK:
                     ans = np.zeros(0, np.uint32)
-                out.append((int(r.tag), int(r.count), int(r.status), float(r.submit_s),
-                            float(r.done_s), ans))
+                out.append((int(r.tag), int(r.count), int(r.status), float(r.arrival_s),
+                            float(r.submit_s), float(r.done_s), ans))
             if n < len(self._res):
                 return out
+
+    def batches(self) -> np.ndarray:
+        """Records of the retired batches (oldest first) as a structured
+        array: slot, queries, answer_values, first_arrival_s, admit_s,
+        launched_s, done_s, retired_s."""
+        buf = (capi.bp_server_batch * 65536)()
+        parts = []
+        while True:
+            n = capi.lib.bp_server_batches(self.ptr, buf, len(buf))
+            if n:
+                parts.append(np.ctypeslib.as_array(buf)[:n].copy())
+            if n < len(buf):
+                break
+        if not parts:
+            return np.ctypeslib.as_array(buf)[:0].copy()
+        return np.concatenate(parts)
 
     def drain(self, timeout_s: float = 120.0) -> None:
         check(capi.lib.bp_server_drain(self.ptr, timeout_s), "bp_server_drain")

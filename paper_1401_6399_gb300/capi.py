@@ -21,7 +21,8 @@ BP_MODE_AUTO, BP_MODE_UNFUSED, BP_MODE_FUSED = 0, 1, 2
 
 class bp_tuning(C.Structure):
     _fields_ = [("dense_blocks", C.c_uint32), ("query_chunk_blocks", C.c_uint32),
-                ("query_warps", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+                ("query_warps", C.c_uint32), ("lookback_spin_limit", C.c_uint32),
+                ("withhold_tile", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 class bp_server_config(C.Structure):
     _fields_ = [("slots", C.c_uint32), ("max_batch_queries", C.c_uint32),
@@ -31,8 +32,14 @@ class bp_server_config(C.Structure):
 
 class bp_server_result(C.Structure):
     _fields_ = [("tag", C.c_uint64), ("count", C.c_uint32), ("status", C.c_int32),
-                ("submit_s", C.c_double), ("done_s", C.c_double),
+                ("arrival_s", C.c_double), ("submit_s", C.c_double), ("done_s", C.c_double),
                 ("answer", C.POINTER(C.c_uint32))]
+
+
+class bp_server_batch(C.Structure):
+    _fields_ = [("slot", C.c_uint32), ("queries", C.c_uint32), ("answer_values", C.c_uint64),
+                ("first_arrival_s", C.c_double), ("admit_s", C.c_double),
+                ("launched_s", C.c_double), ("done_s", C.c_double), ("retired_s", C.c_double)]
 
 
 # struct bp_list (48 bytes)
@@ -90,6 +97,7 @@ _decl("bp_server_replay", _int, _vp, _vp, _vp, _vp, _u32, _vp)
 _decl("bp_server_poll", _u32, _vp, C.POINTER(bp_server_result), _u32)
 _decl("bp_server_drain", _int, _vp, C.c_double)
 _decl("bp_server_stats", _int, _vp, C.POINTER(C.c_uint64))
+_decl("bp_server_batches", _u32, _vp, C.POINTER(bp_server_batch), _u32)
 _decl("bp_server_destroy", None, _vp)
 _decl("bp_get_tuning", _int, C.POINTER(bp_tuning))
 _decl("bp_set_tuning", _int, C.POINTER(bp_tuning))
@@ -239,13 +247,15 @@ def bp_get_tuning() -> dict:
     t = bp_tuning()
     check(lib.bp_get_tuning(C.byref(t)), "bp_get_tuning")
     return {"dense_blocks": t.dense_blocks, "query_chunk_blocks": t.query_chunk_blocks,
-            "query_warps": t.query_warps}
+            "query_warps": t.query_warps, "lookback_spin_limit": t.lookback_spin_limit,
+            "withhold_tile": t.withhold_tile}
 
 
 def bp_set_tuning(**kw) -> None:
     cur = bp_get_tuning()
     cur.update(kw)
-    t = bp_tuning(cur["dense_blocks"], cur["query_chunk_blocks"], cur["query_warps"])
+    t = bp_tuning(cur["dense_blocks"], cur["query_chunk_blocks"], cur["query_warps"],
+                  cur["lookback_spin_limit"], cur["withhold_tile"])
     check(lib.bp_set_tuning(C.byref(t)), "bp_set_tuning")
 
 

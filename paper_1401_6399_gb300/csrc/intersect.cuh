@@ -416,7 +416,7 @@ __device__ __forceinline__ uint64_t tile_base(uint32_t count, uint32_t t, bool l
     }
     const uint32_t run = __shfl_sync(kFull, inc, kIxWarps - 1);
     if (lane < kIxWarps) s_wcnt[lane] = inc - c;
-    const uint32_t P = lookback_exclusive_warp(cp.state, t, run, to.status, lane);
+    const uint32_t P = lookback_exclusive_warp(cp, t, run, to.status, lane);
     if (lane == 0) {
       s_base[0] = P;
       if (last_tile) {

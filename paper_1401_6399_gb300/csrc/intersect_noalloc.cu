@@ -36,7 +36,8 @@ constexpr uint64_t kNoAllocMaxTiles = (kNoAllocScratchBytes - 16) / 8;
 static_assert(kNoAllocMaxTiles * kIxWarps * 128 == BP_NOALLOC_MAX_SHORT_LIST,
               "header limit out of step with the scratch array");
 
-// Device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch, looked up once per device and kept
+// for the life of the CUDA context (a cudaDeviceReset invalidates it).
 std::mutex g_mu;
 void *g_addr[64] = {nullptr};
 
@@ -62,9 +63,10 @@ struct NoAllocArgs {
   uint32_t nf;
 };
 
-// Same work as the fused pair kernel of bp_intersect_pair: the shorter list
-// r block by block, the longer list f through its skip headers, ordered
-// output by ticketed tiles and look-back.
+// The intersection of the fused pair kernel of bp_intersect_pair on a fixed
+// schedule: one block of the shorter list r per warp (no run-length choice,
+// no window of f kept from run to run), the longer list f through its skip
+// headers, ordered output by ticketed tiles and look-back.
 __global__ void __launch_bounds__(kIxThreads)
     noalloc_pair_kernel(NoAllocArgs a, Compaction cp, TileOut to, uint32_t ntiles,
                         uint32_t dense_max) {

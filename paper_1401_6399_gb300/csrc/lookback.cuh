@@ -6,14 +6,16 @@
 // Tile state word (u64): flag << 32 | value; flag 1 = the tile's own count,
 // 2 = inclusive count of all tiles up to it.  The words and the ticket live
 // in caller scratch and are zeroed by the host before each launch.  Every
-// wait is bounded: after kSpinLimit polls it records BP_ERR_TIMEOUT and
-// proceeds as if the missing tile had no output.
+// wait is bounded: after `spin_limit` polls (kLookbackSpinLimit unless the
+// tuning sets another) it records BP_ERR_TIMEOUT and proceeds as if the
+// missing tile had no output.  For testing that path the tuning can name a
+// tile that publishes nothing (Compaction::withhold), so that the tiles
+// after it run out of polls.
 #pragma once
 #include "common.cuh"
+#include "tuning.h"
 
 namespace bp {
-
-constexpr uint32_t kLookbackSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
   uint64_t v;
@@ -30,14 +32,25 @@ __device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
 // nearest tiles not yet accounted for (lane i: tile top - i), adds their
 // counts down to the nearest inclusive one and stops there, or moves 32
 // tiles back.
-__device__ __forceinline__ uint32_t lookback_exclusive_warp(uint64_t *state, uint32_t t,
+// Scratch of one compaction: ticket counter + one state word per tile, and
+// the limits of the look-back's waits.
+struct Compaction {
+  uint32_t *ticket;
+  uint64_t *state;
+  uint32_t spin_limit;  // polls of one state word before giving up
+  uint32_t withhold;    // tile that publishes nothing (testing), or UINT32_MAX
+};
+
+__device__ __forceinline__ uint32_t lookback_exclusive_warp(const Compaction &cp, uint32_t t,
                                                            uint32_t agg, uint32_t *status,
                                                            int lane) {
+  uint64_t *state = cp.state;
+  const bool publish = t != cp.withhold;
   if (t == 0) {
-    if (lane == 0) st_release_u64(state, (2ull << 32) | agg);
+    if (lane == 0 && publish) st_release_u64(state, (2ull << 32) | agg);
     return 0;
   }
-  if (lane == 0) st_release_u64(state + t, (1ull << 32) | agg);
+  if (lane == 0 && publish) st_release_u64(state + t, (1ull << 32) | agg);
   uint32_t excl = 0;
   for (int64_t top = (int64_t)t - 1; top >= 0; top -= 32) {
     const int64_t j = top - lane;
@@ -45,7 +58,7 @@ __device__ __forceinline__ uint32_t lookback_exclusive_warp(uint64_t *state, uin
     if (j >= 0) {
       uint32_t spins = 0;
       while (((s = ld_acquire_u64(state + j)) >> 32) == 0) {
-        if (++spins > kLookbackSpinLimit) break;
+        if (++spins > cp.spin_limit) break;
         __nanosleep(64);
       }
     }
@@ -59,15 +72,9 @@ __device__ __forceinline__ uint32_t lookback_exclusive_warp(uint64_t *state, uin
     excl += __reduce_add_sync(kFull, lane <= stop ? (uint32_t)s : 0u);
     if (incl) break;
   }
-  if (lane == 0) st_release_u64(state + t, (2ull << 32) | (excl + agg));
+  if (lane == 0 && publish) st_release_u64(state + t, (2ull << 32) | (excl + agg));
   return excl;
 }
-
-// Scratch of one compaction: ticket counter + one state word per tile.
-struct Compaction {
-  uint32_t *ticket;
-  uint64_t *state;
-};
 
 __host__ __device__ inline size_t compaction_bytes(uint64_t ntiles) { return 16 + 8 * ntiles; }
 
@@ -75,6 +82,7 @@ inline Compaction compaction_at(void *p) {
   Compaction c;
   c.ticket = static_cast<uint32_t *>(p);
   c.state = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(p) + 16);
+  lookback_limits(c.spin_limit, c.withhold);
   return c;
 }
 

@@ -14,6 +14,13 @@
 // So requests that arrive while other batches are on the GPU are admitted as
 // soon as a slot and its memory are free, and several batches run on the
 // device at once.  Nothing here allocates device or pinned memory.
+//
+// The shared arrival queue is held only for moves: the dispatcher takes
+// everything queued into a backlog of its own in one step and sizes batches
+// from there, so submitters (up to a million per second) never wait for an
+// admission decision.  Each query carries the time it was due (its scheduled
+// arrival under replay) besides the time it was queued, and latency counts
+// from the former.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -39,7 +46,7 @@ inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Pending {
   uint64_t tag;
-  double submit_s;
+  double arrival_s, submit_s;
   uint32_t k;
   uint32_t terms[64];
 };
@@ -48,9 +55,11 @@ struct Done {
   uint64_t tag;
   uint32_t count;
   int32_t status;
-  double submit_s, done_s;
+  double arrival_s, submit_s, done_s;
   std::vector<uint32_t> answer;
 };
+
+constexpr size_t kBatchRecords = 1u << 20;  // timeline entries kept
 
 struct Slot {
   cudaStream_t stream;
@@ -73,6 +82,7 @@ struct Slot {
   // the batch in flight
   std::vector<Pending> batch;
   uint64_t out_cap = 0;
+  bp_server_batch rec{};
 };
 
 }  // namespace
@@ -89,17 +99,22 @@ struct bp_server {
 
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Pending> queue;
+  std::deque<Pending> queue;    // shared with the submitters (under mu)
+  std::deque<Pending> backlog;  // the dispatcher's own, in arrival order
+  std::atomic<uint64_t> backlog_size{0};
   std::deque<Done> done;
   std::vector<Done> polled;  // answers handed out by the last poll
+  std::deque<bp_server_batch> records;  // retired batches (under mu)
   uint64_t submitted = 0, completed = 0, batches = 0, rejected = 0, max_busy = 0;
   std::atomic<bool> stop{false};
   std::thread worker;
   int first_error = BP_OK;
 
   void run();
-  bool admit(Slot &s);
+  void take_arrivals();
+  bool admit(Slot &s, uint32_t slot_index);
   void retire(Slot &s);
+  int submit_at(uint64_t tag, const uint32_t *terms, uint32_t k, double arrival_s);
 };
 
 namespace {
@@ -115,56 +130,70 @@ void slot_layout(const bp_server_config &c, size_t &fixed_dev, size_t &fixed_hos
 
 }  // namespace
 
-bool bp_server::admit(Slot &s) {
-  // take queries from the head of the queue while they fit the slot
+void bp_server::take_arrivals() {
+  std::lock_guard<std::mutex> g(mu);
+  if (queue.empty()) return;
+  if (backlog.empty()) {
+    backlog.swap(queue);
+  } else {
+    for (auto &p : queue) backlog.push_back(p);
+    queue.clear();
+  }
+  backlog_size.store(backlog.size());
+}
+
+bool bp_server::admit(Slot &s, uint32_t slot_index) {
+  // take queries from the head of the backlog while they fit the slot
+  const double t_admit = now_s();
   std::vector<Pending> take;
+  std::vector<Done> rejects;
   std::vector<uint32_t> terms;
   std::vector<uint64_t> toff(1, 0);
   uint64_t cap = 0, items = 0;
-  {
-    std::lock_guard<std::mutex> g(mu);
-    while (!queue.empty() && take.size() < cfg.max_batch_queries) {
-      const Pending &p = queue.front();
-      uint64_t nmin = 0, qitems = 0;
-      if (p.k) {
-        nmin = UINT64_MAX;
-        const bp_list *drv = &h_lists[p.terms[0]];
-        for (uint32_t i = 0; i < p.k; i++) {
-          const bp_list &L = h_lists[p.terms[i]];
-          nmin = std::min<uint64_t>(nmin, L.n);
-          // the list that drives the query: compressed before bitmaps, then shortest
-          const bool lb = L.layout == BP_LAYOUT_BITMAP, db = drv->layout == BP_LAYOUT_BITMAP;
-          if (lb < db || (lb == db && L.n < drv->n)) drv = &L;
-        }
-        qitems = bp::query_items_of(*drv);
+  while (!backlog.empty() && take.size() < cfg.max_batch_queries) {
+    const Pending &p = backlog.front();
+    uint64_t nmin = 0, qitems = 0;
+    if (p.k) {
+      nmin = UINT64_MAX;
+      const bp_list *drv = &h_lists[p.terms[0]];
+      for (uint32_t i = 0; i < p.k; i++) {
+        const bp_list &L = h_lists[p.terms[i]];
+        nmin = std::min<uint64_t>(nmin, L.n);
+        // the list that drives the query: compressed before bitmaps, then shortest
+        const bool lb = L.layout == BP_LAYOUT_BITMAP, db = drv->layout == BP_LAYOUT_BITMAP;
+        if (lb < db || (lb == db && L.n < drv->n)) drv = &L;
       }
-      // memory this batch would need with p added
-      const uint64_t cap2 = cap + nmin, items2 = items + qitems;
-      const size_t need = bp::query_batch_scratch_for(terms.size() + p.k,
-                                                      (uint32_t)take.size() + 1,
-                                                      std::max<uint64_t>(cap2, 1), items2);
-      const bool fits_dev = need <= slot_dev - fixed_dev;
-      const bool fits_host = 4 * cap2 <= slot_host - fixed_host;
-      if (!fits_dev || !fits_host) {
-        if (take.empty()) {  // can never fit this slot: reject it
-          Done d{p.tag, 0, BP_ERR_SCRATCH, p.submit_s, now_s(), {}};
-          done.push_back(std::move(d));
-          rejected++;
-          completed++;
-          queue.pop_front();
-          continue;
-        }
-        break;
-      }
-      terms.insert(terms.end(), p.terms, p.terms + p.k);
-      toff.push_back(toff.back() + p.k);
-      cap = cap2;
-      items = items2;
-      take.push_back(p);
-      queue.pop_front();
+      qitems = bp::query_items_of(*drv);
     }
+    // memory this batch would need with p added
+    const uint64_t cap2 = cap + nmin, items2 = items + qitems;
+    const size_t need = bp::query_batch_scratch_for(terms.size() + p.k, (uint32_t)take.size() + 1,
+                                                    std::max<uint64_t>(cap2, 1), items2);
+    const bool fits_dev = need <= slot_dev - fixed_dev;
+    const bool fits_host = 4 * cap2 <= slot_host - fixed_host;
+    if (!fits_dev || !fits_host) {
+      if (take.empty()) {  // can never fit this slot: reject it
+        rejects.push_back(Done{p.tag, 0, BP_ERR_SCRATCH, p.arrival_s, p.submit_s, now_s(), {}});
+        backlog.pop_front();
+        continue;
+      }
+      break;
+    }
+    terms.insert(terms.end(), p.terms, p.terms + p.k);
+    toff.push_back(toff.back() + p.k);
+    cap = cap2;
+    items = items2;
+    take.push_back(p);
+    backlog.pop_front();
   }
-  if (take.empty()) return false;
+  backlog_size.store(backlog.size());
+  if (!rejects.empty()) {
+    std::lock_guard<std::mutex> g(mu);
+    for (auto &d : rejects) done.push_back(std::move(d));
+    rejected += rejects.size();
+    completed += rejects.size();
+  }
+  if (take.empty()) return !rejects.empty();
   const uint32_t nq = (uint32_t)take.size();
   std::memcpy(s.h_terms, terms.data(), 4 * terms.size());
   std::memcpy(s.h_toff, toff.data(), 8 * toff.size());
@@ -188,14 +217,18 @@ bool bp_server::admit(Slot &s) {
       (cudaMemcpyAsync(s.h_status, s.d_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
        cudaEventRecord(s.ev, st) != cudaSuccess))
     rc = BP_ERR_CUDA;
+  double first_arrival = take.front().arrival_s;
+  for (const auto &p : take) first_arrival = std::min(first_arrival, p.arrival_s);
+  s.rec = bp_server_batch{slot_index, nq, 0, first_arrival, t_admit, now_s(), 0.0, 0.0};
   s.batch.swap(take);
   s.out_cap = out_cap;
   s.busy = true;
   batches++;
   if (rc != BP_OK) {  // report the launch failure on every query of the batch
+    const double t = now_s();
     std::lock_guard<std::mutex> g(mu);
     if (first_error == BP_OK) first_error = rc;
-    for (auto &p : s.batch) done.push_back(Done{p.tag, 0, rc, p.submit_s, now_s(), {}});
+    for (auto &p : s.batch) done.push_back(Done{p.tag, 0, rc, p.arrival_s, p.submit_s, t, {}});
     completed += s.batch.size();
     s.batch.clear();
     s.busy = false;
@@ -208,19 +241,27 @@ void bp_server::retire(Slot &s) {
   const int st = (int)*s.h_status;
   std::vector<Done> out;
   out.reserve(s.batch.size());
+  uint64_t values = 0;
   for (size_t q = 0; q < s.batch.size(); q++) {
-    Done d{s.batch[q].tag, s.h_counts[q], st, s.batch[q].submit_s, t, {}};
+    const Pending &p = s.batch[q];
+    Done d{p.tag, s.h_counts[q], st, p.arrival_s, p.submit_s, t, {}};
+    values += d.count;
     if (cfg.deliver_answers && st == BP_OK) {
       const uint64_t o = s.h_out_off[q];
       d.answer.assign(s.h_answers + o, s.h_answers + o + d.count);
     }
     out.push_back(std::move(d));
   }
+  s.rec.answer_values = values;
+  s.rec.done_s = t;
+  s.rec.retired_s = now_s();
   {
     std::lock_guard<std::mutex> g(mu);
     for (auto &d : out) done.push_back(std::move(d));
     completed += s.batch.size();
     if (st != BP_OK && first_error == BP_OK) first_error = st;
+    if (records.size() >= kBatchRecords) records.pop_front();
+    records.push_back(s.rec);
   }
   s.batch.clear();
   s.busy = false;
@@ -235,8 +276,9 @@ void bp_server::run() {
         retire(s);
         worked = true;
       }
-    for (auto &s : slots)
-      if (!s.busy && admit(s)) worked = true;
+    take_arrivals();
+    for (uint32_t i = 0; i < slots.size(); i++)
+      if (!slots[i].busy && admit(slots[i], i)) worked = true;
     uint64_t busy = 0;
     for (auto &s : slots) busy += s.busy ? 1 : 0;
     if (busy > max_busy) {
@@ -244,16 +286,35 @@ void bp_server::run() {
       max_busy = busy;
     }
     if (stop.load() && !worked) {
-      bool idle = true;
+      bool idle = backlog.empty();
       for (auto &s : slots) idle &= !s.busy;
       std::lock_guard<std::mutex> g(mu);
       if (idle && queue.empty()) break;
     }
     if (!worked) {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait_for(lk, std::chrono::microseconds(20));
+      if (queue.empty()) cv.wait_for(lk, std::chrono::microseconds(20));
     }
   }
+}
+
+int bp_server::submit_at(uint64_t tag, const uint32_t *terms, uint32_t k, double arrival_s) {
+  if ((k && !terms) || k > cfg.max_terms) return BP_ERR_ARG;
+  for (uint32_t i = 0; i < k; i++)
+    if (terms[i] >= n_terms) return BP_ERR_ARG;
+  Pending p;
+  p.tag = tag;
+  p.k = k;
+  std::memcpy(p.terms, terms, 4ull * k);
+  p.submit_s = now_s();
+  p.arrival_s = arrival_s > 0.0 ? arrival_s : p.submit_s;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    queue.push_back(p);
+    submitted++;
+  }
+  cv.notify_one();
+  return BP_OK;
 }
 
 extern "C" {
@@ -332,21 +393,8 @@ bp_server *bp_server_create(const uint8_t *d_data, const bp_list *d_lists, const
 }
 
 int bp_server_submit(bp_server *s, uint64_t tag, const uint32_t *terms, uint32_t k) {
-  if (!s || (k && !terms) || k > s->cfg.max_terms) return BP_ERR_ARG;
-  for (uint32_t i = 0; i < k; i++)
-    if (terms[i] >= s->n_terms) return BP_ERR_ARG;
-  Pending p;
-  p.tag = tag;
-  p.submit_s = now_s();
-  p.k = k;
-  std::memcpy(p.terms, terms, 4ull * k);
-  {
-    std::lock_guard<std::mutex> g(s->mu);
-    s->queue.push_back(p);
-    s->submitted++;
-  }
-  s->cv.notify_one();
-  return BP_OK;
+  if (!s) return BP_ERR_ARG;
+  return s->submit_at(tag, terms, k, 0.0);
 }
 
 int bp_server_replay(bp_server *s, const uint64_t *tags, const uint32_t *terms,
@@ -357,8 +405,8 @@ int bp_server_replay(bp_server *s, const uint64_t *tags, const uint32_t *terms,
     const double due = t0 + arrival_s[i];
     while (now_s() < due) {
     }
-    const int rc = bp_server_submit(s, tags[i], terms + term_off[i],
-                                    (uint32_t)(term_off[i + 1] - term_off[i]));
+    const int rc = s->submit_at(tags[i], terms + term_off[i],
+                                (uint32_t)(term_off[i + 1] - term_off[i]), due);
     if (rc != BP_OK) return rc;
   }
   return BP_OK;
@@ -379,6 +427,7 @@ uint32_t bp_server_poll(bp_server *s, bp_server_result *out, uint32_t max) {
     out[i].tag = d.tag;
     out[i].count = d.count;
     out[i].status = d.status;
+    out[i].arrival_s = d.arrival_s;
     out[i].submit_s = d.submit_s;
     out[i].done_s = d.done_s;
     out[i].answer = d.answer.empty() ? nullptr : d.answer.data();
@@ -407,8 +456,19 @@ int bp_server_stats(bp_server *s, uint64_t out[6]) {
   out[2] = s->batches;
   out[3] = s->rejected;
   out[4] = s->max_busy;
-  out[5] = s->queue.size();
+  out[5] = s->queue.size() + s->backlog_size.load();
   return BP_OK;
+}
+
+uint32_t bp_server_batches(bp_server *s, bp_server_batch *out, uint32_t max) {
+  if (!s || !out) return 0;
+  std::lock_guard<std::mutex> g(s->mu);
+  uint32_t n = 0;
+  while (n < max && !s->records.empty()) {
+    out[n++] = s->records.front();
+    s->records.pop_front();
+  }
+  return n;
 }
 
 void bp_server_destroy(bp_server *s) {

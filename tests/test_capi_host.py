@@ -198,3 +198,17 @@ def test_scratch_sizes():
     a = capi.bp_decode_scratch_bytes(10**6, capi.BP_LAYOUT_PAPER)
     b = capi.bp_decode_scratch_bytes(2 * 10**6, capi.BP_LAYOUT_PAPER)
     assert 8 * (10**6 // 128) < a < b
+
+
+def test_tuning_round_trip_and_wait_limit_range():
+    old = capi.bp_get_tuning()
+    try:
+        capi.bp_set_tuning(lookback_spin_limit=1 << 10, withhold_tile=3)
+        t = capi.bp_get_tuning()
+        assert t["lookback_spin_limit"] == 1 << 10 and t["withhold_tile"] == 3
+        with pytest.raises(capi.BPError) as e:  # above the default limit
+            capi.bp_set_tuning(lookback_spin_limit=(1 << 22) + 1)
+        assert e.value.code == capi.BP_ERR_ARG
+    finally:
+        capi.bp_set_tuning(**old)
+    assert capi.bp_get_tuning() == old

@@ -1,8 +1,8 @@
 """GPU parity of conjunctive queries (bp_query_batch, bp_query_one) against
 the oracle's Set-vs-Set, bit-exact: a Zipf index with clustered lists,
 queries of 1..8 terms, every tuning choice, CUDA-graph replay with new
-queries, capacity and bad-term handling, and a sample of the full-size
-batched-query workload."""
+queries, capacity and bad-term handling.  The full-size workload is in
+test_gpu_full_size.py."""
 import numpy as np
 import pytest
 
@@ -144,31 +144,6 @@ def test_capacity_and_bad_terms(small_index):
         idx.query_batch(np.array([idx.n_terms + 5], np.uint32), np.array([0, 1], np.uint64),
                         out_cap=10)
     assert e.value.code == capi.BP_ERR_ARG
-
-
-def test_full_size_index_sampled(orc):
-    """The batched-query workload at full size: 2^19 terms over [0, 2^25),
-    Zipf(1) lengths capped at 2^24 (1.5e9 postings), 100,000 queries of 2-5
-    terms; every answer is checked for being sorted and contained in each of
-    its lists' ranges, and 300 sampled queries are compared with the oracle."""
-    lens = W.zipf_lengths(1 << 19, 1_500_000_000, 1 << 24)
-    vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
-    idx = api.Index(vals, offs)
-    terms, toff = W.queries(lens, 100_000, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
-    out, o, c = idx.query_batch(terms, toff, out_cap=1 << 30, on_device=True)
-    print("total answer values", idx.last_total)
-    assert int(o[-1]) == idx.last_total == int(c.astype(np.uint64).sum())
-
-    def answer(q):
-        return api.as_u32(out[int(o[q]):int(o[q]) + int(c[q])])
-
-    rng = np.random.default_rng(1)
-    for q in rng.choice(100_000, 300, replace=False):
-        t = terms[int(toff[q]):int(toff[q + 1])]
-        assert np.array_equal(answer(q), orc.svs(lists_of(vals, offs, t))), q
-    for q in range(0, 100_000, 997):
-        r = answer(q).astype(np.int64)
-        assert np.all(np.diff(r) > 0)
 
 
 @pytest.fixture(scope="module")

@@ -41,15 +41,18 @@ def test_alone_equals_mixed_equals_oracle(orc, index):
         for q in range(n):  # one query at a time
             srv.submit(q, terms[int(toff[q]):int(toff[q + 1])])
             srv.drain()
-            (tag, cnt, st, t0, t1, ans), = srv.poll()
+            (tag, cnt, st, ta, t0, t1, ans), = srv.poll()
+            assert ta == t0 <= t1  # a direct submission arrives when it is queued
             assert tag == q and st == capi.BP_OK and ans.size == cnt
             alone[q] = ans
         # the same queries in an open-loop mix at 200,000 queries/s
         arrivals = W.poisson_arrivals(200_000.0, n, 0x5002)
         srv.replay(np.arange(n) + 1000, terms, toff, arrivals)
         srv.drain()
-        mixed = {tag - 1000: ans for (tag, cnt, st, t0, t1, ans) in srv.poll()}
+        res = srv.poll()
+        mixed = {r[0] - 1000: r[6] for r in res}
         st = srv.stats()
+        recs = srv.batches()
     finally:
         srv.close()
     assert sorted(mixed) == list(range(n))
@@ -60,6 +63,20 @@ def test_alone_equals_mixed_equals_oracle(orc, index):
     assert st["completed"] == st["submitted"] == 2 * n
     assert st["batches"] > n  # alone: one batch each; mixed: several batches
     assert st["max_busy_slots"] >= 2  # batches overlapped on the device
+    # replayed queries are stamped with their scheduled arrival: queued no
+    # earlier than due, answered after both
+    arr = np.array([r[3] for r in res])
+    sub = np.array([r[4] for r in res])
+    done = np.array([r[5] for r in res])
+    assert np.all(sub >= arr) and np.all(done >= sub)
+    order = np.argsort([r[0] for r in res])
+    assert np.all(np.abs(arr[order] - arr[order][0] - (arrivals - arrivals[0])) < 1e-6)
+    # the timeline holds every batch of both phases, in a consistent order
+    assert recs.size == st["batches"]
+    assert int(recs["queries"].sum()) == 2 * n
+    assert np.all(recs["admit_s"] <= recs["launched_s"])
+    assert np.all(recs["launched_s"] <= recs["done_s"])
+    assert np.all(recs["done_s"] <= recs["retired_s"])
 
 
 def test_oversized_query_is_rejected_alone(orc, index):
@@ -77,7 +94,7 @@ def test_oversized_query_is_rejected_alone(orc, index):
         srv.close()
     assert res[1][2] == capi.BP_ERR_SCRATCH
     assert res[2][2] == capi.BP_OK
-    assert np.array_equal(res[2][5], svs(orc, vals, offs, small))
+    assert np.array_equal(res[2][6], svs(orc, vals, offs, small))
 
 
 def test_hybrid_index_served(orc):
@@ -93,7 +110,7 @@ def test_hybrid_index_served(orc):
     try:
         srv.replay(np.arange(n), terms, toff, W.poisson_arrivals(100_000.0, n, 0x5102))
         srv.drain()
-        got = {tag: (st, ans) for (tag, cnt, st, t0, t1, ans) in srv.poll()}
+        got = {r[0]: (r[2], r[6]) for r in srv.poll()}
     finally:
         srv.close()
     assert sorted(got) == list(range(n))

@@ -436,3 +436,22 @@ def test_svs_against_python_sets(orc):
         for L in lists[1:]:
             want &= set(L.tolist())
         assert orc.svs(lists).tolist() == sorted(want)
+
+
+def test_svs_gallop_against_python_sets(orc):
+    """The galloping Set-vs-Set used on sets with very long lists: the same
+    unique answer as Python's set intersection, including skewed sets (one
+    list 1000x longer), empty lists and a single list."""
+    rng = np.random.default_rng(12)
+    for trial in range(40):
+        k = int(rng.integers(1, 7))
+        sizes = [int(rng.integers(0, 400)) for _ in range(k)]
+        if trial % 3 == 0:
+            sizes[int(rng.integers(0, k))] = 200_000
+        lists = [_sorted_distinct(rng, s, 1 << 18) for s in sizes]
+        want = set(lists[0].tolist())
+        for L in lists[1:]:
+            want &= set(L.tolist())
+        assert orc.svs_gallop(lists).tolist() == sorted(want)
+        assert orc.svs_gallop(lists).tolist() == orc.svs(lists).tolist()
+    assert orc.svs_gallop([]).size == 0

@@ -2,9 +2,10 @@
 allocate device memory (a plug-in limited to the buffers it is given, a
 server whose pool already holds all device memory, latency-bound code that
 must not call cudaMalloc).  It keeps its scratch in a fixed array of device
-memory owned by the library.  Its answers must equal those of
-bp_intersect_pair, value for value, on consecutive calls (which reuse that
-array and must each clear it).  The file name makes pytest collect it last."""
+memory owned by the library.  Its answers must equal the oracle's
+intersection and those of bp_intersect_pair, value for value, on consecutive
+calls (which reuse that array and must each clear it).  The file name makes
+pytest collect it last."""
 import ctypes as C
 
 import numpy as np
@@ -52,14 +53,16 @@ def pairs():
     return out
 
 
-def test_matches_intersect_pair_on_consecutive_calls():
+def test_matches_intersect_pair_on_consecutive_calls(orc):
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for r, f in pairs():
             er = api.to_device(capi.bp_encode(r, capi.BP_LAYOUT_GPU, nthreads=8))
             ef = api.to_device(capi.bp_encode(f, capi.BP_LAYOUT_GPU, nthreads=8))
-            want = api.as_u32(api.intersect_pair(er, r.size, ef, f.size, capi.BP_LAYOUT_GPU,
-                                                 capi.BP_MODE_FUSED, stream=s))
+            want = orc.intersect(r, f)
+            fused = api.as_u32(api.intersect_pair(er, r.size, ef, f.size, capi.BP_LAYOUT_GPU,
+                                                  capi.BP_MODE_FUSED, stream=s))
+            assert np.array_equal(fused, want)
             for _ in range(2):  # two calls in a row share the library's array
                 rc, out, cnt, st = noalloc(er, r.size, ef, f.size, s)
                 assert rc == capi.BP_OK
@@ -72,6 +75,30 @@ def test_matches_intersect_pair_on_consecutive_calls():
             s.synchronize()
             assert rc == capi.BP_OK and int(st.item()) == capi.BP_OK
             assert np.array_equal(api.as_u32(out[: int(cnt.item())]), want)
+
+
+def test_empty_list_and_empty_intersection(orc):
+    """An empty list in either argument gives an empty answer; disjoint lists
+    with the shorter one second give an empty answer too."""
+    s = torch.cuda.Stream()
+    f = W.uniform(50_000, 0, 1 << 20, 0x6200)
+    ef = api.to_device(capi.bp_encode(f, capi.BP_LAYOUT_GPU, nthreads=8))
+    empty = np.zeros(0, np.uint32)
+    ee = api.to_device(capi.bp_encode(empty, capi.BP_LAYOUT_GPU))
+    for a, b in ((ee, ef), (ef, ee)):
+        na = 0 if a is ee else f.size
+        nb = 0 if b is ee else f.size
+        rc, out, cnt, st = noalloc(a, na, b, nb, s)
+        s.synchronize()
+        assert rc == capi.BP_OK and int(st.item()) == capi.BP_OK and int(cnt.item()) == 0
+    f_even = np.unique(f & ~np.uint32(1))  # even values only
+    g = np.unique(f[:3000] | np.uint32(1))   # odd values only: disjoint from f_even
+    assert orc.intersect(g, f_even).size == 0
+    ev = api.to_device(capi.bp_encode(f_even, capi.BP_LAYOUT_GPU, nthreads=8))
+    eg = api.to_device(capi.bp_encode(g, capi.BP_LAYOUT_GPU, nthreads=8))
+    rc, out, cnt, st = noalloc(ev, f_even.size, eg, g.size, s)  # shorter list second
+    s.synchronize()
+    assert rc == capi.BP_OK and int(st.item()) == capi.BP_OK and int(cnt.item()) == 0
 
 
 def test_rejects_a_shorter_list_beyond_the_limit():
