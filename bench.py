@@ -482,6 +482,26 @@ def pair_sweep(stream, reps: int, cpu_threads: int = 0):
                 e1.synchronize()
                 tot += e0.elapsed_time(e1)
             row[name + "_us"] = round(1e3 * tot / reps, 2)
+            if mode == capi.BP_MODE_FUSED:  # the same call with the merge regime off
+                saved = capi.bp_get_tuning()
+                capi.bp_set_tuning(merge_span=0)
+                try:
+                    call()
+                    tot = 0.0
+                    for _ in range(reps):
+                        with torch.cuda.stream(stream):
+                            flush.zero_()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        call()
+                        e1.record(stream)
+                        e1.synchronize()
+                        tot += e0.elapsed_time(e1)
+                    assert int(st.item()) == 0 and torch.equal(res[:k], answers["fused"])
+                finally:
+                    capi.bp_set_tuning(**saved)
+                row["fused_no_merge_us"] = round(1e3 * tot / reps, 2)
         assert torch.equal(answers["fused"], answers["unfused"])
         cand = np.unique(np.searchsorted(first, r.astype(np.int64), side="right") - 1)
         cand = cand[cand >= 0]
@@ -869,6 +889,21 @@ def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
         out["engine"] = srv.stats()
     finally:
         srv.close()
+    # the offline rate on the same 2-8-term mix (first 50,000 queries of the
+    # 1M/s run), answers on the device: what the engine saturates against
+    import torch
+    import workloads as W
+    terms, toff = W.queries(lens, 1_000_000, W.CLUEWEB_TERM_WEIGHTS_2_8, 2, 0x5000 + 1_000_000)
+    nq = 50_000
+    terms, toff = terms[: int(toff[nq])], toff[: nq + 1]
+    _, o, _ = idx.query_batch(terms, toff, out_cap=1 << 31, on_device=True)
+    stream = torch.cuda.Stream()
+    ms, res, _, _ = graph_batch(idx, terms, toff, int(o[-1]), stream, 3)
+    del res
+    torch.cuda.empty_cache()
+    out["offline_same_mix"] = {"queries": nq, "ms_per_batch": round(ms, 3),
+                               "queries_per_s": round(nq / (ms * 1e-3), 1),
+                               "answer_values": int(o[-1])}
     return out
 
 
@@ -1204,7 +1239,9 @@ def main():
         import __graft_entry__ as ge
         ge.build()
         stream = torch.cuda.Stream()
-        print(json.dumps({"pair_sweep": pair_sweep(stream, reps=args.steps)}), flush=True)
+        print(json.dumps({"pair_sweep": pair_sweep(stream, reps=args.steps),
+                          "pair_batch_64": pair_batch(stream, reps=max(3, args.steps))}),
+              flush=True)
         return
     if args.serving_sweep:
         import torch

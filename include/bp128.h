@@ -141,6 +141,12 @@ typedef enum {
  * headers (skewed lengths, the galloping regime).  query_chunk_blocks is the
  * number of blocks of a query's shortest list per work item in
  * bp_query_batch, query_warps the warps per CTA of its persistent kernel.
+ * merge_span selects the merge regime for similar lengths: a run of the
+ * shorter list whose value range covers at most merge_span blocks of the
+ * longer list per block of its own is intersected by merging the decoded
+ * runs (Section 6's merge, split over a warp's lanes by merge path) instead
+ * of by searching; 0 turns the merge regime off.  In bp_query_batch it
+ * applies to the first list a query's candidates meet.
  *
  * The last two fields bound and test the waits of the ordered output of
  * bp_intersect_pair (each CTA, in ticket order, waits for the output counts
@@ -157,7 +163,8 @@ typedef struct bp_tuning {
   uint32_t query_warps;         /* 4 or 8, default 8 */
   uint32_t lookback_spin_limit; /* 0 (default 2^22) or 1..2^22 */
   uint32_t withhold_tile;       /* 0 (none), or 1 + the tile to withhold */
-  uint32_t reserved[3];
+  uint32_t merge_span;          /* 0 (off, the default) or 1..64 */
+  uint32_t reserved[2];
 } bp_tuning;
 
 /* Status text for a bp_status code (static string, never NULL). */

@@ -2,9 +2,9 @@
 
 Measures every candidate of the tuning space (skew threshold between the
 dense and sparse regimes, blocks of the shortest list per work item, warps
-per CTA of the persistent query kernel) on a sample of the caller's own
-workload, installs the fastest with bp_set_tuning, and records the choice in
-a JSON file keyed by GPU name.  Every candidate gives the same answers (the
+per CTA of the persistent query kernel, span limit of the merge regime) on
+a sample of the caller's own workload, installs the fastest with
+bp_set_tuning, and records the choice in a JSON file keyed by GPU name.  Every candidate gives the same answers (the
 tests check this); only speed differs.
 """
 from __future__ import annotations
@@ -23,6 +23,7 @@ SPACE = {
     "dense_blocks": (1, 2, 4, 8),
     "query_chunk_blocks": (1, 2, 4, 8),
     "query_warps": (4, 8),
+    "merge_span": (0, 2, 4, 16),
 }
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "tuning.json")
@@ -67,9 +68,9 @@ def tune_queries(index, terms: np.ndarray, term_off: np.ndarray, reps: int = 3,
     stream = torch.cuda.Stream()
     old = capi.bp_get_tuning()
     results = {}
-    for db, ch, wp in itertools.product(space["dense_blocks"], space["query_chunk_blocks"],
-                                        space["query_warps"]):
-        capi.bp_set_tuning(dense_blocks=db, query_chunk_blocks=ch, query_warps=wp)
+    keys = list(space)
+    for combo in itertools.product(*(space[k] for k in keys)):
+        capi.bp_set_tuning(**dict(zip(keys, combo)))
         sb = capi.bp_query_batch_scratch_bytes(index.h_lists, terms, term_off, cap)
         scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
 
@@ -77,18 +78,18 @@ def tune_queries(index, terms: np.ndarray, term_off: np.ndarray, reps: int = 3,
             index.query_batch_async(d_terms, d_off, nq, int(term_off[-1]), out, out_off, counts,
                                     scratch, st, stream)
 
-        results[(db, ch, wp)] = _time_ms(run, reps, stream)
+        results[combo] = _time_ms(run, reps, stream)
         del scratch
     stream.synchronize()
     if int(st.item()) != 0:
         capi.bp_set_tuning(**old)
         raise capi.BPError(int(st.item()), "autotune")
     best = min(results, key=results.get)
-    params = {"dense_blocks": best[0], "query_chunk_blocks": best[1], "query_warps": best[2]}
+    params = dict(zip(keys, best))
     capi.bp_set_tuning(**params)
     if save_cache:
         save(params, results)
-    return {"best": params, "ms": {f"{k[0]},{k[1]},{k[2]}": round(v, 4)
+    return {"best": params, "ms": {",".join(str(x) for x in k): round(v, 4)
                                    for k, v in results.items()}}
 
 

@@ -22,7 +22,8 @@ BP_MODE_AUTO, BP_MODE_UNFUSED, BP_MODE_FUSED = 0, 1, 2
 class bp_tuning(C.Structure):
     _fields_ = [("dense_blocks", C.c_uint32), ("query_chunk_blocks", C.c_uint32),
                 ("query_warps", C.c_uint32), ("lookback_spin_limit", C.c_uint32),
-                ("withhold_tile", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("withhold_tile", C.c_uint32), ("merge_span", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
 
 class bp_server_config(C.Structure):
     _fields_ = [("slots", C.c_uint32), ("max_batch_queries", C.c_uint32),
@@ -248,14 +249,14 @@ def bp_get_tuning() -> dict:
     check(lib.bp_get_tuning(C.byref(t)), "bp_get_tuning")
     return {"dense_blocks": t.dense_blocks, "query_chunk_blocks": t.query_chunk_blocks,
             "query_warps": t.query_warps, "lookback_spin_limit": t.lookback_spin_limit,
-            "withhold_tile": t.withhold_tile}
+            "withhold_tile": t.withhold_tile, "merge_span": t.merge_span}
 
 
 def bp_set_tuning(**kw) -> None:
     cur = bp_get_tuning()
     cur.update(kw)
     t = bp_tuning(cur["dense_blocks"], cur["query_chunk_blocks"], cur["query_warps"],
-                  cur["lookback_spin_limit"], cur["withhold_tile"])
+                  cur["lookback_spin_limit"], cur["withhold_tile"], cur["merge_span"])
     check(lib.bp_set_tuning(C.byref(t)), "bp_set_tuning")
 
 

@@ -32,16 +32,20 @@ struct PairArgs {
 };
 
 // Shared memory per warp: up to 8 decoded blocks of r (survivors compacted
-// in place), then the dense window of f.
+// in place), the window of f, and one hit bit per value of r (merge regime).
 constexpr int kPairGroups = 8;
-constexpr int kPairWarpWords = kPairGroups * 128 + kIxDenseMax * 128;
+constexpr int kPairWarpWords = kPairGroups * 128 + kIxDenseMax * 128 + kPairGroups * 4;
 
 // vpw: values of the shorter list per warp: a power of two 8..128 (a slice
-// of one block, for very skewed pairs) or 128 g for g = 1..8 blocks, which
-// the warp filters run by run with its window of f moving forward.
-__global__ void __launch_bounds__(kIxThreads)
+// of one block, for very skewed pairs) or 128 g for g = 1..8 blocks.  A run
+// whose value range covers at most merge_span blocks of f per block of r
+// (similar densities) is merged with those blocks of f (merge_run_hits);
+// otherwise the warp filters it 128 values at a time with its window of f
+// moving forward (dense) or by per-value probes (sparse).  merge_span = 0
+// turns the merge regime off.
+__global__ void __launch_bounds__(kIxThreads, 3)
     fused_pair_kernel(PairArgs a, Compaction cp, TileOut to, uint32_t ntiles, uint32_t dense_max,
-                      uint32_t vpw) {
+                      uint32_t vpw, uint32_t merge_span) {
   extern __shared__ uint32_t smem[];
   __shared__ uint32_t s_wcnt[kIxWarps], s_base[1], s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(cp.ticket, 1u);
@@ -50,6 +54,7 @@ __global__ void __launch_bounds__(kIxThreads)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t *s_r = smem + w * kPairWarpWords;
   uint32_t *s_f = s_r + kPairGroups * 128;
+  uint32_t *s_hit = s_f + kIxDenseMax * 128;
 
   GlView R, F;
   bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
@@ -66,10 +71,11 @@ __global__ void __launch_bounds__(kIxThreads)
     const uint64_t p1 = min((uint64_t)a.nr, p0 + vpw);       // one past the last
     const uint32_t kb0 = (uint32_t)(p0 >> 7), ng = (uint32_t)(((p1 - 1) >> 7) - kb0 + 1);
     // bit 4g+j of `alive`: value 32j + lane of block kb0+g is in the range
-    uint32_t alive = 0;
+    uint32_t alive = 0, na = 0;
     for (uint32_t g = 0; g < ng; g++) {
       const uint32_t cnt = gl_block_into(R, kb0 + g, s_r + 128u * g, lane, to.status);
       const uint64_t bstart = 128ull * (kb0 + g);
+      na = 128u * g + cnt;  // every block but r's last is full
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         const uint64_t pos = bstart + 32 * j + lane;
@@ -77,8 +83,26 @@ __global__ void __launch_bounds__(kIxThreads)
       }
     }
     __syncwarp();
+    bool merged = false;
+    if (merge_span != 0u && na > 0u && F.nblocks > 0u) {
+      const int64_t kl = warp_ubound(F.first, F.nblocks, s_r[na - 1], lane);
+      if (kl < 0) {  // the whole run is below f's first value
+        alive = 0;
+        merged = true;
+      } else {
+        const int64_t kf = warp_ubound(F.first, F.nblocks, s_r[0], lane);
+        if ((uint64_t)(kl - imax64(kf, 0) + 1) <= (uint64_t)merge_span * ng) {
+          s_hit[lane] = 0u;
+          __syncwarp();
+          merge_run_hits(F, s_r, na, kf, kl, s_f, s_hit, lane, to.status);
+          alive = alive_and_hits(alive, ng, s_hit, lane);
+          __syncwarp();
+          merged = true;
+        }
+      }
+    }
     FWin win = fwin_empty();
-    for (uint32_t g = 0; g < ng; g++) {
+    for (uint32_t g = 0; g < ng && !merged; g++) {
       uint32_t v[4];
       bool valid[4], hit[4];
       uint32_t lo = 0xFFFFFFFFu, hi = 0u;
@@ -99,19 +123,7 @@ __global__ void __launch_bounds__(kIxThreads)
       for (int j = 0; j < 4; j++)
         if (valid[j] && !hit[j]) alive &= ~(1u << (4 * g + j));
     }
-    // compact the survivors, in order, to the front of s_r
-    for (uint32_t g = 0; g < ng; g++) {
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const bool a = (alive >> (4 * g + j)) & 1u;
-        const uint32_t x = s_r[128u * g + 32 * j + lane];
-        const uint32_t m = __ballot_sync(kFull, a);
-        __syncwarp();
-        if (a) s_r[scount + __popc(m & lanemask_lt())] = x;
-        scount += __popc(m);
-        __syncwarp();
-      }
-    }
+    scount = compact_alive(s_r, ng, alive, lane);  // the survivors, in order
   }
   tile_emit_buf(s_r, scount, t, t == ntiles - 1, cp, to, s_wcnt, s_base);
 }
@@ -238,7 +250,7 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
     const uint32_t ft = pair_tiles(a.nr, vpw);
     if (cudaMemsetAsync(sp, 0, compaction_bytes(ft), s) != cudaSuccess) return BP_ERR_CUDA;
     fused_pair_kernel<<<ft, kIxThreads, kPairSmem, s>>>(
-        a, cp, to, ft, std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw);
+        a, cp, to, ft, std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw, tu.merge_span);
     return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
   }
   // unfused: decode both lists into scratch, then intersect the arrays

@@ -389,6 +389,150 @@ __device__ __forceinline__ void gl_membership_win(const GlView &f, const uint32_
   __syncwarp();
 }
 
+// ---- merge regime (similar lengths; Section 6's scalar merge, split over
+// the lanes of a warp by merge path) ----
+
+// Smallest i in [lo, hi) with s[i] >= v (hi if none): warp-cooperative
+// 32-way search over a sorted shared-memory array; v is warp-uniform.
+__device__ __forceinline__ uint32_t smem_lbound_warp(const uint32_t *s, uint32_t lo, uint32_t hi,
+                                                     uint32_t v, int lane) {
+  while (hi - lo > 32) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t p = lo + (uint32_t)lane * step;
+    const bool lt = p < hi && s[p] < v;
+    const uint32_t cnt = __popc(__ballot_sync(kFull, lt));
+    if (cnt == 0) return lo;
+    const uint32_t nlo = lo + (cnt - 1) * step + 1;
+    hi = min(hi, lo + cnt * step);
+    lo = nlo;
+  }
+  const bool lt = lo + lane < hi && s[lo + lane] < v;
+  return lo + __popc(__ballot_sync(kFull, lt));
+}
+
+// Intersection of two sorted runs in shared memory, A[0..na) and B[0..nb)
+// (distinct values within each), by merging: the merged sequence (A before B
+// on ties) is cut into 32 equal parts, each lane finds where its part starts
+// by binary search on the cross diagonal and merges it.  When A[i] is taken,
+// every B before the next one not yet taken is below A[i], so A[i] is in B
+// exactly when that next B equals it.  Sets bit abase + i of `hits` for each
+// such A[i].
+__device__ __forceinline__ void merge_path_hits(const uint32_t *A, uint32_t na, const uint32_t *B,
+                                                uint32_t nb, uint32_t *hits, uint32_t abase,
+                                                int lane) {
+  const uint32_t T = na + nb;
+  const uint32_t per = (T + 31) >> 5;
+  const uint32_t d0 = min((uint32_t)lane * per, T), d1 = min(d0 + per, T);
+  uint32_t lo = d0 > nb ? d0 - nb : 0u, hi = min(d0, na);  // A's share of the first d0
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (A[mid] <= B[d0 - mid - 1]) lo = mid + 1;
+    else hi = mid;
+  }
+  uint32_t i = lo, j = d0 - lo;
+  uint32_t a = i < na ? A[i] : 0u, b = j < nb ? B[j] : 0u;
+  // one step per merged value, without branches: the lanes take A or B
+  // independently, so a branch per side would run both sides every step
+  for (uint32_t s = d0; s < d1; s++) {
+    const bool take_a = i < na && (j >= nb || a <= b);
+    if (take_a && j < nb && a == b)
+      atomicOr(hits + ((abase + i) >> 5), 1u << ((abase + i) & 31u));
+    const uint32_t ni = i + (take_a ? 1u : 0u), nj = j + (take_a ? 0u : 1u);
+    const bool in = take_a ? ni < na : nj < nb;
+    const uint32_t x = in ? (take_a ? A[ni] : B[nj]) : 0u;
+    a = take_a ? x : a;
+    b = take_a ? b : x;
+    i = ni;
+    j = nj;
+  }
+}
+
+// Which values of a warp's sorted run A[0..na) (shared memory) are in GL
+// list f.  kfirst: the block of f holding A[0] (-1 if A[0] is below f's
+// first value); klast >= 0: the block holding A[na-1].  f's blocks between
+// them are decoded window by window (up to kIxDenseMax blocks into smem) and
+// each window is merged with the part of A inside its value range.  A window
+// ends before the block that holds the first value of A beyond it, so no
+// block is decoded twice.  Sets bit i of `hits` (zeroed by the caller) for
+// each A[i] in f.  Kept out of line: one copy of its code per kernel, away
+// from the hot loops of the other regimes.
+static __device__ __noinline__ void merge_run_hits(const GlView &f, const uint32_t *A, uint32_t na,
+                                                      int64_t kfirst, int64_t klast, uint32_t *smem,
+                                                      uint32_t *hits, int lane, uint32_t *status) {
+  uint32_t a0 = 0;
+  int64_t klo = kfirst;
+  if (kfirst < 0) {  // values below f's first one cannot match
+    a0 = smem_lbound_warp(A, 0, na, __ldg(f.first), lane);
+    if (a0 >= na) return;
+    klo = warp_ubound(f.first, f.nblocks, A[a0], lane);
+  }
+  while (true) {
+    const int64_t khi = klo + kIxDenseMax - 1 < klast ? klo + kIxDenseMax - 1 : klast;
+    uint32_t len = 0;
+    for (int64_t k = klo; k <= khi; k++) {
+      const uint32_t i = (uint32_t)(k - klo);
+      const uint32_t c = gl_block_into(f, (uint32_t)k, smem + 128u * i, lane, status);
+      len = 128u * i + c;
+      if (c < 128u) break;  // only f's last block is short (or a corrupt one)
+    }
+    __syncwarp();
+    const bool more = khi + 1 < (int64_t)f.nblocks;
+    const uint32_t a1 = more ? smem_lbound_warp(A, a0, na, __ldg(f.first + khi + 1), lane) : na;
+    const uint32_t b0 = smem_lbound_warp(smem, 0, len, A[a0], lane);
+    merge_path_hits(A + a0, a1 - a0, smem + b0, len - b0, hits, a0, lane);
+    __syncwarp();
+    if (a1 >= na || !more) return;
+    klo = fwd_ubound(f.first, f.nblocks, A[a1], khi + 1, lane);  // f.first[khi+1] <= A[a1]
+    a0 = a1;
+  }
+}
+
+// Candidate bookkeeping of a warp's run in shared memory: bit 4g + j of
+// `alive` (lane-held) stands for position 128g + 32j + lane.
+
+// The alive mask of a run whose first na positions are all candidates.
+__device__ __forceinline__ uint32_t alive_prefix(uint32_t na, int lane) {
+  uint32_t alive = 0;
+  for (uint32_t g = 0; 128u * g < na; g++) {
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      if (128u * g + 32u * j + (uint32_t)lane < na) alive |= 1u << (4 * g + j);
+  }
+  return alive;
+}
+
+// The alive mask restricted to the positions whose bit is set in `hits`
+// (one bit per position, shared memory).
+__device__ __forceinline__ uint32_t alive_and_hits(uint32_t alive, uint32_t ng,
+                                                   const uint32_t *hits, int lane) {
+  for (uint32_t g = 0; g < ng; g++) {
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      if (!((hits[4 * g + j] >> lane) & 1u)) alive &= ~(1u << (4 * g + j));
+  }
+  return alive;
+}
+
+// Move the alive values of the ng groups of s_r, in order, to its front;
+// returns how many there are.
+__device__ __forceinline__ uint32_t compact_alive(uint32_t *s_r, uint32_t ng, uint32_t alive,
+                                                  int lane) {
+  uint32_t count = 0;
+  for (uint32_t g = 0; g < ng; g++) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const bool a = (alive >> (4 * g + j)) & 1u;
+      const uint32_t x = s_r[128u * g + 32 * j + lane];
+      const uint32_t m = __ballot_sync(kFull, a);
+      __syncwarp();
+      if (a) s_r[count + __popc(m & lanemask_lt())] = x;
+      count += __popc(m);
+      __syncwarp();
+    }
+  }
+  return count;
+}
+
 // Ordered output of one tile (all threads of the CTA call it).  Lane holds
 // positions 32k + lane of its warp's chunk; chunks are in warp order.
 struct TileOut {

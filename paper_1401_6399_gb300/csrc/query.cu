@@ -34,8 +34,8 @@ namespace {
 constexpr int kMaxTerms = 64;
 constexpr int kMaxChunk = 8;
 // per warp: the item's decoded blocks (survivors are compacted in place),
-// then the dense window of the list being searched
-constexpr int kWarpSmemWords = kMaxChunk * 128 + kIxDenseMax * 128;
+// the dense window of the list being searched, one hit bit per candidate
+constexpr int kWarpSmemWords = kMaxChunk * 128 + kIxDenseMax * 128 + kMaxChunk * 4;
 
 inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -323,17 +323,21 @@ __device__ __forceinline__ void bitmap_and_item(const uint8_t *__restrict__ data
 // true for batches with bitmap terms (hybrid index); the plan kernel records
 // which, and the other instance leaves at once.  The bitmap code would cost
 // the all-compressed kernel registers (measured: about 4 % of its speed).
-template <bool HYB>
+// MERGE: the instance with the merge regime for a query's first list, run
+// when the tuning's merge_span is not 0; its call costs the kernel about
+// 7 % where it is not taken (measured), so it is not compiled in otherwise.
+template <bool HYB, bool MERGE>
 __global__ void __launch_bounds__(256, 3)
     q_main_kernel(const uint8_t *__restrict__ data, const bp_list *__restrict__ lists,
                               const uint64_t *__restrict__ toff, uint32_t nq, QScratch sc,
                               uint32_t max_items, uint64_t arena_cap, uint32_t chunk,
-                              uint32_t dense_max, uint32_t *status) {
+                              uint32_t dense_max, uint32_t merge_span, uint32_t *status) {
   if ((sc.counters[2] != 0ull) != HYB) return;
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t *s_r = smem + w * kWarpSmemWords;
   uint32_t *s_f = s_r + kMaxChunk * 128;
+  uint32_t *s_hit = s_f + kIxDenseMax * 128;
   const uint32_t total = sc.base[nq];
   if (total > max_items) {  // the caller's scratch holds fewer work items
     if (threadIdx.x == 0 && blockIdx.x == 0) set_status(status, BP_ERR_SCRATCH);
@@ -361,11 +365,12 @@ __global__ void __launch_bounds__(256, 3)
       // the item's candidates, ascending, in s_r: `chunk` blocks of the
       // shortest compressed list; bit 4g+j of `alive`: value 128g + 32j +
       // lane is still a candidate
-      uint32_t alive = 0;
+      uint32_t alive = 0, na = 0;
       const uint32_t b0 = c * chunk, b1 = min(V1.gl.nblocks, b0 + chunk);
       const uint32_t ng = b1 > b0 ? b1 - b0 : 0u;
       for (uint32_t g = 0; g < ng; g++) {
         const uint32_t cnt = gl_block_into(V1.gl, b0 + g, s_r + 128u * g, lane, status);
+        na = 128u * g + cnt;
 #pragma unroll
         for (int j = 0; j < 4; j++)
           if ((uint32_t)(32 * j + lane) < cnt) alive |= 1u << (4 * g + j);
@@ -384,6 +389,24 @@ __global__ void __launch_bounds__(256, 3)
         if (HYB && F.bitmap) {
           alive = bitmap_filter(F.gl.payload, F.gl.pw, s_r, ng, alive, lane);
           continue;
+        }
+        if (MERGE && t == 1 && F.gl.nblocks > 0u && na > 0u) {
+          // merge regime for the first list, while the candidates are the
+          // whole decoded run s_r[0..na)
+          const int64_t kl = warp_ubound(F.gl.first, F.gl.nblocks, s_r[na - 1], lane);
+          if (kl < 0) {  // every candidate is below the list's first value
+            alive = 0;
+            continue;
+          }
+          const int64_t kf = warp_ubound(F.gl.first, F.gl.nblocks, s_r[0], lane);
+          if ((uint64_t)(kl - imax64(kf, 0) + 1) <= (uint64_t)merge_span * ng) {
+            s_hit[lane] = 0u;
+            __syncwarp();
+            merge_run_hits(F.gl, s_r, na, kf, kl, s_f, s_hit, lane, status);
+            alive = alive_and_hits(alive, ng, s_hit, lane);
+            __syncwarp();
+            continue;
+          }
         }
         FWin win = fwin_empty();
         for (uint32_t g = 0; g < ng; g++) {
@@ -589,21 +612,29 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BP_ERR_CUDA;
     std::lock_guard<std::mutex> g(g_main_mu);
     if (!((g_main_smem_set >> dev) & 1u)) {
-      if (cudaFuncSetAttribute(q_main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess ||
-          cudaFuncSetAttribute(q_main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(sizeof(uint32_t) * kWarpSmemWords * 8)) != cudaSuccess)
+      const int bytes = (int)(sizeof(uint32_t) * kWarpSmemWords * 8);
+      if (cudaFuncSetAttribute(q_main_kernel<false, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(q_main_kernel<true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(q_main_kernel<false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+          cudaFuncSetAttribute(q_main_kernel<true, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return BP_ERR_CUDA;
       g_main_smem_set |= 1ull << dev;
     }
   }
+  // the instances for this tuning: compressed-only and hybrid, with or
+  // without the merge regime
+  const bool mrg = tu.merge_span != 0u;
+  auto *const kc = mrg ? q_main_kernel<false, true> : q_main_kernel<false, false>;
+  auto *const kh = mrg ? q_main_kernel<true, true> : q_main_kernel<true, false>;
   int per_sm = 0, per_sm_h = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_main_kernel<false>, threads,
-                                                    smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kc, threads, smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, q_main_kernel<true>, threads,
-                                                    smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, kh, threads, smem) != cudaSuccess ||
       per_sm_h < 1)
     per_sm_h = 1;
   const int grid = per_sm * device_sm_count(), grid_h = per_sm_h * device_sm_count();
@@ -611,10 +642,10 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
                                                   status);
   scan_u32_kernel<<<1, 1024, 0, s>>>(sc.base, nq);
   const uint32_t dense = std::min<uint32_t>(tu.dense_blocks, kIxDenseMax);
-  q_main_kernel<false><<<grid, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items,
-                                                   arena_cap, chunk, dense, status);
-  q_main_kernel<true><<<grid_h, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items,
-                                                    arena_cap, chunk, dense, status);
+  kc<<<grid, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items, arena_cap, chunk, dense,
+                                 tu.merge_span, status);
+  kh<<<grid_h, threads, smem, s>>>(data, lists, term_off, nq, sc, max_items, arena_cap, chunk,
+                                   dense, tu.merge_span, status);
   const int cgrid = (int)std::min<uint64_t>((nq + 7) / 8, 65535);
   q_count_kernel<<<cgrid, 256, 0, s>>>(nq, sc, max_items, counts);
   scan_counts_kernel<<<1, 1024, 0, s>>>(counts, nq, out_off, out_cap, status);

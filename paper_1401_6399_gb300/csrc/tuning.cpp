@@ -6,7 +6,7 @@
 namespace bp {
 namespace {
 std::mutex g_mu;
-Tuning g_tuning = {4u, 1u, 8u, 0u, 0u, {0, 0, 0}};
+Tuning g_tuning = {4u, 1u, 8u, 0u, 0u, 0u, {0, 0}};
 }  // namespace
 
 const Tuning &tuning() { return g_tuning; }
@@ -34,6 +34,7 @@ int bp_set_tuning(const bp_tuning *in) {
   if (in->query_chunk_blocks < 1 || in->query_chunk_blocks > 8) return BP_ERR_ARG;
   if (in->query_warps != 4 && in->query_warps != 8) return BP_ERR_ARG;
   if (in->lookback_spin_limit > bp::kLookbackSpinLimit) return BP_ERR_ARG;
+  if (in->merge_span > 64u) return BP_ERR_ARG;
   std::lock_guard<std::mutex> g(bp::g_mu);
   bp::g_tuning = *in;
   return BP_OK;

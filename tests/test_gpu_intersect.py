@@ -55,11 +55,30 @@ def test_ratio_sweep_full_size(orc, long_list, m, layout, mode):
     assert np.array_equal(gpu_intersect(r, f, layout, mode), want)
 
 
-@pytest.mark.parametrize("dense", [1, 2, 4, 8])
-def test_every_regime_threshold_gives_the_same_result(orc, dense):
+@pytest.mark.parametrize("m", [1 << 22, 1 << 18, 1 << 14])
+@pytest.mark.parametrize("merge_span", [0, 1, 64])
+def test_ratio_sweep_merge_regime_on_and_off(orc, long_list, m, merge_span):
+    """The fused path of the ratio sweep with the merge regime off (0), only
+    for runs of equal density (1), and for every run within 64 blocks of f
+    per block of r."""
+    f = long_list
+    k = round(0.1 * m)
+    r = W.pair_short(f, m, k, 1 << 26, 0x3000 + m)
+    want = orc.intersect(r, f)
     old = capi.bp_get_tuning()
     try:
-        capi.bp_set_tuning(dense_blocks=dense)
+        capi.bp_set_tuning(merge_span=merge_span)
+        got = gpu_intersect(r, f, capi.BP_LAYOUT_GPU, capi.BP_MODE_FUSED)
+    finally:
+        capi.bp_set_tuning(**old)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("dense,merge_span", [(1, 0), (2, 4), (4, 0), (4, 4), (8, 64), (8, 1)])
+def test_every_regime_threshold_gives_the_same_result(orc, dense, merge_span):
+    old = capi.bp_get_tuning()
+    try:
+        capi.bp_set_tuning(dense_blocks=dense, merge_span=merge_span)
         f = W.clustered(300_000, 0, 1 << 26, 0x77)
         for m in (300_000, 30_000, 3_000, 300, 30):
             r = W.pair_short(f, m, m // 3, 1 << 26, m)

@@ -62,12 +62,14 @@ def test_batch_single_and_degenerate_queries(orc, small_index):
     check_all(orc, idx, vals, offs, terms, toff, res)
 
 
-@pytest.mark.parametrize("dense,chunk,warps", [(1, 1, 8), (8, 8, 4), (2, 3, 8), (4, 1, 4)])
-def test_every_tuning_gives_the_same_answers(orc, small_index, dense, chunk, warps):
+@pytest.mark.parametrize("dense,chunk,warps,merge", [(1, 1, 8, 0), (8, 8, 4, 4), (2, 3, 8, 64),
+                                                     (4, 1, 4, 1), (4, 8, 8, 0), (8, 8, 8, 64)])
+def test_every_tuning_gives_the_same_answers(orc, small_index, dense, chunk, warps, merge):
     idx, vals, offs = small_index
     old = capi.bp_get_tuning()
     try:
-        capi.bp_set_tuning(dense_blocks=dense, query_chunk_blocks=chunk, query_warps=warps)
+        capi.bp_set_tuning(dense_blocks=dense, query_chunk_blocks=chunk, query_warps=warps,
+                           merge_span=merge)
         terms, toff = queries(np.diff(offs), 800, 0x4A02 + dense)
         res = idx.query_batch(terms, toff)
         check_all(orc, idx, vals, offs, terms, toff, res)
