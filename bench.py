@@ -65,11 +65,16 @@ def parse_args():
                    help="run only the batched-query measurement (for profiling)")
     p.add_argument("--query-scale", type=int, default=1,
                    help="with --queries-only: index and batch this many times smaller")
+    p.add_argument("--profile-queries", type=int, default=0,
+                   help="with --profile-case queries: only the first N queries of the batch")
     p.add_argument("--serving-sweep", action="store_true",
                    help="only the serving engine at 1M queries/s offered over slot counts "
                         "and batch sizes")
-    p.add_argument("--profile-case", choices=["decode_sum", "gp_decode", "pl_decode"],
-                   help="time one small decode case alone (for ncu): 4 lists of 2^26")
+    p.add_argument("--profile-case",
+                   choices=["decode", "decode_sum", "gp_decode", "pl_decode", "pair", "queries"],
+                   help="time one case of one kernel alone (for ncu): the decodes on 4 lists "
+                        "of 2^26, the fused pair on m = n = 2^22, the batched queries on the "
+                        "index --query-scale times smaller")
     return p.parse_args()
 
 
@@ -1200,17 +1205,57 @@ def run_ours(args, rank, world, local):
 
 
 def profile_case(args) -> dict:
-    """A small case of one decode kernel, launched warmup + steps times on
-    its own (the command ncu captures): 4 lists of 2^26 uniform integers,
-    more than L2 in and out."""
+    """One kernel's case, launched warmup + steps times on its own (the
+    command ncu captures).  Decodes: 4 lists of 2^26 uniform integers, more
+    than L2 in and out.  pair: the fused intersection of the m = n = 2^22
+    pair of the sweep, L2 flushed before each call.  queries: the batched
+    queries (default tuning) on the index --query-scale times smaller."""
     import torch
     import __graft_entry__ as ge
     ge.build()
     from paper_1401_6399_gb300 import api, capi
+    if args.profile_case == "pair":
+        import workloads as W
+        f = W.uniform(1 << 22, 0, 1 << 26, 0x3000)
+        r = W.pair_short(f, 1 << 22, round(0.1 * (1 << 22)), 1 << 26, 0x3000 + (1 << 22))
+        er = api.to_device(capi.bp_encode(r, capi.BP_LAYOUT_GPU, nthreads=8))
+        ef = api.to_device(capi.bp_encode(f, capi.BP_LAYOUT_GPU, nthreads=8))
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.Stream()
+        tot = 0.0
+        for i in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = api.intersect_pair(er, r.size, ef, f.size, capi.BP_LAYOUT_GPU,
+                                     capi.BP_MODE_FUSED, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                tot += e0.elapsed_time(e1)
+        assert res.numel() == round(0.1 * (1 << 22))
+        return {"profile_case": "pair", "us": round(1e3 * tot / args.steps, 2)}
+    if args.profile_case == "queries":
+        import workloads as W
+        sc = args.query_scale
+        lens = W.zipf_lengths((1 << 19) // sc, 1_500_000_000 // sc, (1 << 24) // sc)
+        vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
+        idx = api.Index(vals, offs)
+        terms, toff = W.queries(lens, 100_000 // sc, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
+        if args.profile_queries:  # a sample: the first N queries of the batch
+            nq = min(args.profile_queries, toff.size - 1)
+            terms, toff = terms[: int(toff[nq])], toff[: nq + 1]
+        _, o, _ = idx.query_batch(terms, toff, out_cap=1 << 31, on_device=True)
+        stream = torch.cuda.Stream()
+        ms, _, _, _ = graph_batch(idx, terms, toff, int(o[-1]), stream, args.steps)
+        return {"profile_case": "queries", "scale": sc, "queries": int(toff.size - 1),
+                "ms": round(ms, 4), "queries_per_s": round((toff.size - 1) / (ms * 1e-3), 1)}
     n, L = 1 << args.log2n, 4
     lists = make_lists("uniform", L, n, UNIVERSE, SEED_BASE)
-    layout = {"decode_sum": capi.BP_LAYOUT_GPU, "gp_decode": capi.BP_LAYOUT_PFOR,
-              "pl_decode": capi.BP_LAYOUT_PAPER}[args.profile_case]
+    layout = {"decode": capi.BP_LAYOUT_GPU, "decode_sum": capi.BP_LAYOUT_GPU,
+              "gp_decode": capi.BP_LAYOUT_PFOR, "pl_decode": capi.BP_LAYOUT_PAPER}[args.profile_case]
     batch = api.ListBatch(encode_all(lists, layout), [n] * L, layout)
     stream = torch.cuda.Stream()
     status = api.status_tensor()

@@ -19,18 +19,24 @@
 //          from its entry and records the byte offset and width of each block.
 //  rest    pl_leftover reads the fewer than 16 blocks after the meta-blocks
 //          (one width byte each) and checks the stream's size.
-//  seeds   pl_units<kColsum> sums the deltas of each column over chunks of
-//          kChunk work units; a segmented exclusive scan over the chunks
-//          (every list restarts from zero) gives each chunk its seed.
-//  decode  pl_units<kStore|kSum> unpacks every block (Algorithm 1, 4-lane
-//          interleave) and adds the running column seed; pl_tail decodes the
-//          varint tail (Section 4.1) from the last packed value.
+//  decode  pl_onepass takes chunks of kOpC work units in ticket order.  A
+//          warp stages a chunk's blocks in shared memory with one bulk copy,
+//          unpacks each block once (Algorithm 1, 4-lane interleave) into a
+//          value buffer in shared memory, with running column sums that
+//          restart at every list head, and publishes the chunk's column sums.
+//          The seed of the chunk -- the column sums of its list's earlier
+//          blocks (Section 5) -- comes from a decoupled look-back over the
+//          chunks before it; the values are then stored with the seed added.
+//          So the compressed stream is read once here (and once by parse).
+//          pl_tail decodes the varint tail (Section 4.1) from the last packed
+//          value.
 //
 // Work unit u of a list: its block u - unit_base, then one unit for the tail.
 #include "decode.h"
 #include "bulk.cuh"
 #include "gl_block.cuh"
 #include "pl_block.cuh"
+#include "tuning.h"
 
 namespace bp {
 
@@ -42,11 +48,11 @@ constexpr uint32_t kEnt = 513;      // lines where a chain can enter a segment
 constexpr uint32_t kGrp = 8;        // segments per group
 constexpr uint32_t kLiveCap = 256;  // live lines kept per segment for pl_emit
 constexpr uint32_t kMapChunk = 16;  // group maps staged at a time by pl_resolve
-constexpr uint32_t kChunk = 32;     // work units per seed chunk
-constexpr uint32_t kScanPer = 16;   // chunks per thread in the chunk scan
-constexpr uint32_t kScanTile = kThreads * kScanPer;
-constexpr int kUnitMinBlocks = 5;  // resident CTAs per SM for pl_units (<= 51 registers)
-constexpr uint32_t kStageBytes = 4096;  // per warp of pl_units: a chunk's blocks at b <= 7
+constexpr uint32_t kChunk = 32;          // work units per warp and tile step
+constexpr int kTileChunks = 7;           // chunk warps per CTA of pl_tiles (+ a control warp)
+constexpr int kTileThreads = 32 * (kTileChunks + 1);
+constexpr int kTileMinBlocks = 4;        // resident CTAs per SM for pl_tiles
+constexpr uint32_t kStageBytes = 3840;   // per warp and buffer: 32 blocks of average width <= 7.5
 constexpr uint64_t kOffMask = (1ull << 56) - 1;
 constexpr uint64_t kBadEntry = ~0ull;  // width byte 0xFF: no block to decode
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -85,21 +91,23 @@ struct PlScratch {
   uint32_t *grp_entry;  // [groups] entry line offset of the true chain (kNone: off it)
   uint32_t *grp_mbase;  // [groups] meta-blocks before the group
   uint32_t *list_qm;    // [count] line after the last meta-block; 0: the list is bad
-  uint4 *chunk;         // [chunks] column sums, then seeds
-  uint32_t *chunk_head; // [chunks] a list starts inside the chunk
-  uint4 *tile;          // [tiles] segmented tile sums, then tile seeds
-  uint32_t *tile_head;  // [tiles]
+  // look-back state of pl_tiles, one set per instance (D4 lists, other kinds):
+  unsigned long long *op_ticket;  // [2] next tile
+  uint32_t *op_flag;    // [2][tiles] 0 nothing yet, 1 aggregate, 2 inclusive
+  uint4 *op_agg;        // [2][tiles] column sums of the tile since its last list head
+  uint4 *op_inc;        // [2][tiles] the same from the first block of the tile's last list
   uint32_t *lastval;    // [count] last packed value of each list
 };
 
 struct PlLayout {
   size_t boffw, seg_base, grp_base, ctl, seg_in, live, live_cnt, grp_map, grp_entry, grp_mbase,
-      list_qm, chunk, chunk_head, tile, tile_head, lastval, total;
+      list_qm, op_ticket, op_flag, op_agg, op_inc, lastval, total;
 };
 
 PlLayout pl_layout(uint64_t units, uint32_t count) {
   const uint64_t S = max_segs(units, count), G = max_groups(units, count);
-  const uint64_t nch = (units + kChunk - 1) / kChunk, nt = (nch + kScanTile - 1) / kScanTile;
+  const uint64_t nch = (units + kChunk - 1) / kChunk;
+  const uint64_t ntl = (nch + kTileChunks - 1) / kTileChunks;  // tiles
   size_t o = 0;
   auto take = [&o](size_t bytes) {
     const size_t r = o;
@@ -118,10 +126,10 @@ PlLayout pl_layout(uint64_t units, uint32_t count) {
   L.grp_entry = take(4 * G);
   L.grp_mbase = take(4 * G);
   L.list_qm = take(4 * (size_t)count);
-  L.chunk = take(16 * nch);
-  L.chunk_head = take(4 * nch);
-  L.tile = take(16 * nt);
-  L.tile_head = take(4 * nt);
+  L.op_ticket = take(16);  // the flags follow: one memset clears tickets and flags
+  L.op_flag = take(8 * ntl);
+  L.op_agg = take(32 * ntl);
+  L.op_inc = take(32 * ntl);
   L.lastval = take(4 * (size_t)count);
   L.total = o;
   return L;
@@ -141,12 +149,23 @@ PlScratch carve(void *scratch, const PlLayout &L) {
   sc.grp_entry = reinterpret_cast<uint32_t *>(b + L.grp_entry);
   sc.grp_mbase = reinterpret_cast<uint32_t *>(b + L.grp_mbase);
   sc.list_qm = reinterpret_cast<uint32_t *>(b + L.list_qm);
-  sc.chunk = reinterpret_cast<uint4 *>(b + L.chunk);
-  sc.chunk_head = reinterpret_cast<uint32_t *>(b + L.chunk_head);
-  sc.tile = reinterpret_cast<uint4 *>(b + L.tile);
-  sc.tile_head = reinterpret_cast<uint32_t *>(b + L.tile_head);
+  sc.op_ticket = reinterpret_cast<unsigned long long *>(b + L.op_ticket);
+  sc.op_flag = reinterpret_cast<uint32_t *>(b + L.op_flag);
+  sc.op_agg = reinterpret_cast<uint4 *>(b + L.op_agg);
+  sc.op_inc = reinterpret_cast<uint4 *>(b + L.op_inc);
   sc.lastval = reinterpret_cast<uint32_t *>(b + L.lastval);
   return sc;
+}
+
+// The look-back state of the second pl_tiles instance (lists of the other
+// kinds): the upper halves of the state arrays.
+__host__ __device__ inline PlScratch sc_other(const PlScratch &sc, uint64_t ntiles) {
+  PlScratch o = sc;
+  o.op_ticket = sc.op_ticket + 1;
+  o.op_flag = sc.op_flag + ntiles;
+  o.op_agg = sc.op_agg + ntiles;
+  o.op_inc = sc.op_inc + ntiles;
+  return o;
 }
 
 __device__ __forceinline__ uint32_t rd_u32(const uint8_t *p) {
@@ -587,13 +606,9 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// ---- column sums and decode over chunks of work units -----------------------------------
+// ---- decode in one pass over tiles of work units ------------------------------------------
 
 enum { kColsum = 0, kStore = 1, kSum = 2 };
-
-__device__ __forceinline__ uint32_t comp(const uint4 &v, int s) {
-  return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
-}
 
 __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane) {
 #pragma unroll
@@ -602,9 +617,6 @@ __device__ __forceinline__ void flush_sum(uint64_t &acc, uint64_t *dst, int lane
   acc = 0;
 }
 
-// Blocks j .. j+run-1 of a fully staged chunk, all of width B (pk of lane
-// u: the block's offset in the stage | width << 16).  Column sums, or the
-// decode with the running seed `carry`, stored through `o` or summed into acc.
 // The values before a block, for each kind of Section 5, from the running
 // column sums C_s of the deltas of the list's earlier blocks (lane 8s+c
 // holds C_s in `carry`): D4 x[-4+s] = C_s; DM and D1 x[-1] = C_3 or
@@ -628,6 +640,80 @@ __device__ __forceinline__ uint32_t kind_last(uint32_t kind, uint32_t carry) {
   if (kind == kD2) return c1 + c3;
   if (kind == kD1) return c0 + c1 + c2 + c3;
   return c3;  // D4 and DM: position 128 nb - 1 is in column 3
+}
+
+// Kind of differential coding of a list (header word 3; lists whose header
+// is bad are marked bad and never decoded).  The column sums need none.
+template <int MODE>
+__device__ __forceinline__ uint32_t list_kind(const uint8_t *data, const bp_list &L) {
+  if (MODE == kColsum || L.enc_bytes < 16) return kD4;
+  const uint32_t k = rd_u32(data + L.enc_offset + 12);
+  return k <= 3u ? k : kD4;
+}
+
+__device__ __forceinline__ uint32_t comp(const uint4 &v, int s) {
+  return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ uint4 add4(const uint4 &a, const uint4 &b) {
+  return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Publish the state of tile t: its column sums `v` as an aggregate (flag 1:
+// its first list continues from earlier tiles) or as the inclusive sums of
+// its last list (flag 2).  Aggregates and inclusive sums are kept apart, so
+// a reader that saw flag 1 never reads a later inclusive value.  One thread.
+__device__ __forceinline__ void tile_publish(const PlScratch &sc, uint64_t t, uint32_t flag,
+                                             const uint4 &v) {
+  __stcg(flag == 2u ? sc.op_inc + t : sc.op_agg + t, v);
+  st_release_u32(sc.op_flag + t, flag);
+}
+
+// Column sums of tile t's first list over all tiles before t (decoupled
+// look-back by one warp): each step reads the 32 nearest tiles not yet
+// accounted for, adds their aggregates down to the nearest inclusive sums
+// and stops there, or moves 32 tiles back.  Every poll is bounded; on
+// timeout it records BP_ERR_TIMEOUT and goes on with what it has.
+__device__ __forceinline__ uint4 tile_lookback(const PlScratch &sc, uint64_t t,
+                                               uint32_t spin_limit, uint32_t *status, int lane) {
+  uint4 excl = make_uint4(0, 0, 0, 0);
+  for (int64_t top = (int64_t)t - 1; top >= 0; top -= 32) {
+    const int64_t j = top - lane;
+    uint32_t f = 2u;  // before tile 0: inclusive sums of zero
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (j >= 0) {
+      uint32_t spins = 0;
+      while ((f = ld_acquire_u32(sc.op_flag + j)) == 0u) {
+        if (++spins > spin_limit) break;
+        __nanosleep(64);
+      }
+      if (f == 1u) v = __ldcg(sc.op_agg + j);
+      else if (f == 2u) v = __ldcg(sc.op_inc + j);
+    }
+    if (__any_sync(kFull, f == 0u)) {
+      if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
+      break;
+    }
+    const uint32_t incl = __ballot_sync(kFull, f == 2u);
+    const int stop = incl ? __ffs(incl) - 1 : 31;
+    const bool take = lane <= stop;
+    excl.x += __reduce_add_sync(kFull, take ? v.x : 0u);
+    excl.y += __reduce_add_sync(kFull, take ? v.y : 0u);
+    excl.z += __reduce_add_sync(kFull, take ? v.z : 0u);
+    excl.w += __reduce_add_sync(kFull, take ? v.w : 0u);
+    if (incl) break;
+  }
+  return excl;
 }
 
 template <int B, int MODE, int KIND>
@@ -708,334 +794,325 @@ __device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int la
   }
 }
 
-// Kind of differential coding of a list (header word 3; lists whose header
-// is bad are marked bad and never decoded).  The column-sum pass needs none.
-template <int MODE>
-__device__ __forceinline__ uint32_t list_kind(const uint8_t *data, const bp_list &L) {
-  if (MODE == kColsum || L.enc_bytes < 16) return kD4;
-  const uint32_t k = rd_u32(data + L.enc_offset + 12);
-  return k <= 3u ? k : kD4;
+
+// A warp's chunk of kChunk work units and how much of it sits in the stage.
+struct Chunk {
+  uint64_t u0;
+  uint32_t cnt;
+  uint64_t eL;      // lane j < cnt: boffw of unit u0 + j
+  uint32_t staged;  // leading units whose blocks are in the stage
+  uint64_t st0;     // stream offset of the stage's first byte
+};
+
+// Stage the chunk's leading blocks of its first list: they lie back to back
+// in the meta-block region, 16-byte aligned, only width lines between them,
+// so one bulk copy brings them in when they fit.  False if the copy's wait
+// ran out (recorded; the copy has landed or given up when this returns).
+__device__ __forceinline__ bool stage_chunk(const uint8_t *data, const ListSrc &src,
+                                            const PlScratch &sc, uint64_t ch,
+                                            uint64_t total_units, int lane, uint32_t bar,
+                                            uint32_t sbase, uint32_t &phase, Chunk &cx,
+                                            uint32_t *status) {
+  cx.u0 = ch * kChunk;
+  cx.cnt = total_units - cx.u0 < kChunk ? (uint32_t)(total_units - cx.u0) : kChunk;
+  cx.eL = (uint32_t)lane < cx.cnt ? sc.boffw[cx.u0 + lane] : kBadEntry;
+  cx.staged = 0;
+  cx.st0 = 0;
+  const uint32_t li = src.find(cx.u0);
+  const bp_list L = src.get(li);
+  const uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+  const uint64_t k0 = cx.u0 - L.unit_base, nb0 = L.n / 128u;
+  uint64_t m = nb0 > k0 ? nb0 - k0 : 0;
+  if (m > cx.cnt) m = cx.cnt;
+  if (m > nxt - cx.u0) m = nxt - cx.u0;
+  const uint64_t offl = cx.eL & kOffMask;
+  const uint32_t bl = (uint32_t)(cx.eL >> 56);
+  const bool fit = __all_sync(kFull, (uint32_t)lane >= m || (bl <= 32u && (offl & 15u) == 0));
+  if (m > 0 && fit) {
+    const uint64_t st0 = __shfl_sync(kFull, offl, 0);
+    const uint64_t bytes = __shfl_sync(kFull, offl + 16ull * bl, (int)m - 1) - st0;
+    if (bytes > 0 && bytes <= kStageBytes) {
+      if (lane == 0) bulk_load(bar, sbase, data + L.enc_offset + st0, (uint32_t)bytes);
+      const bool done = bulk_wait(bar, phase);
+      phase ^= 1u;
+      if (!__all_sync(kFull, done)) {  // record it and let the copy land (bounded)
+        if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
+        bulk_wait(bar, phase ^ 1u);
+        return false;
+      }
+      cx.staged = (uint32_t)m;
+      cx.st0 = st0;
+    }
+  }
+  return true;
 }
 
-// Lane l = 8s + c owns column s, rows 4c..4c+3 of each block (positions
-// 16c + 4j + s); `carry` is the running column sum C_s of the deltas of the
-// list's earlier blocks, from which each kind's seed follows (kind_seed).
-// The decode passes come in two kernels: OTHER = false decodes the D4 lists
-// and passes over the rest, OTHER = true the DM, D2 and D1 lists (each keeps
-// a register allocation of its own); the column-sum pass takes every kind.
-template <int MODE, bool OTHER = false>
-__global__ void __launch_bounds__(kThreads, kUnitMinBlocks)
-    pl_units(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
-             uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t *status) {
-  if (sc.ctl[0] || (OTHER && !sc.ctl[1])) return;
-  const int lane = threadIdx.x & 31, s = lane >> 3, c = lane & 7;
-  const uint64_t warp = (blockIdx.x * (uint64_t)kThreads + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * kThreads) >> 5;
-  const uint64_t nch = (total_units + kChunk - 1) / kChunk;
-  __shared__ __align__(128) uint8_t s_stage[kThreads / 32][kStageBytes];
-  __shared__ __align__(8) uint64_t s_bar[kThreads / 32];
-  const uint32_t bar = smem_addr(&s_bar[threadIdx.x >> 5]);
-  const uint32_t sbase = smem_addr(&s_stage[threadIdx.x >> 5][0]);
-  uint32_t phase = 0;
-  if (lane == 0) bulk_bar_init(bar);
-  __syncwarp();
-  uint64_t acc = 0;
-  uint32_t acc_list = kNone;
-  for (uint64_t ch = warp; ch < nch; ch += nwarps) {
-    const uint64_t u0 = ch * kChunk;
-    const uint32_t cnt = total_units - u0 < kChunk ? (uint32_t)(total_units - u0) : kChunk;
-    const uint64_t eL = (uint32_t)lane < cnt ? sc.boffw[u0 + lane] : kBadEntry;
-    uint32_t li = src.find(u0);
-    bp_list L = src.get(li);
-    uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
-    uint32_t kind = list_kind<MODE>(data, L);
-    // a chunk of one list of the other kernel's kind: nothing to do here
-    if (MODE != kColsum && u0 + cnt <= nxt && (kind != kD4) != OTHER) continue;
-    // The chunk's leading blocks of list li (lanes [0, m)) lie back to back in
-    // the meta-block region, 16-byte aligned, only width lines between them:
-    // stage them in shared memory with one bulk copy when they fit.
-    uint32_t staged = 0;
-    uint64_t st0 = 0;
-    {
-      const uint64_t k0 = u0 - L.unit_base, nb0 = L.n / 128u;
-      uint64_t m = nb0 > k0 ? nb0 - k0 : 0;
-      if (m > cnt) m = cnt;
-      if (m > nxt - u0) m = nxt - u0;
-      if (MODE != kColsum && (kind != kD4) != OTHER) m = 0;  // not this kernel's list
-      const uint64_t offl = eL & kOffMask;
-      const uint32_t bl = (uint32_t)(eL >> 56);
-      const bool fit = __all_sync(kFull, (uint32_t)lane >= m || (bl <= 32u && (offl & 15u) == 0));
-      if (m > 0 && fit) {
-        st0 = __shfl_sync(kFull, offl, 0);
-        const uint64_t bytes = __shfl_sync(kFull, offl + 16ull * bl, (int)m - 1) - st0;
-        if (bytes > 0 && bytes <= kStageBytes) {
-          if (lane == 0) bulk_load(bar, sbase, data + L.enc_offset + st0, (uint32_t)bytes);
-          const bool done = bulk_wait(bar, phase);
-          phase ^= 1u;
-          if (!__all_sync(kFull, done)) {  // give up: record it, let the copy land, stop
-            if (lane == 0) set_status(status, BP_ERR_TIMEOUT);
-            bulk_wait(bar, phase ^ 1u);
-            return;
-          }
-          staged = (uint32_t)m;
-        }
-      }
+// The chunk's units, once the stage is filled.  MODE kColsum: `carry` ends
+// as this lane's part of the column sums of the chunk's last list within the
+// chunk (from its head if it starts here: `head`).  MODE kStore / kSum: the
+// blocks of lists of this instance's kind (D4, or the others if OTHER) are
+// decoded with the running column sums `carry` (the chunk's seed on entry;
+// the same in the 8 lanes of a column), stored or summed; a list's tail unit
+// records its last packed value.
+template <int MODE, bool OTHER>
+__device__ __forceinline__ void chunk_units(const uint8_t *data, const ListSrc &src,
+                                            const PlScratch &sc, const Chunk &cx,
+                                            uint32_t *out, uint64_t *sums, uint32_t sbase,
+                                            int lane, uint32_t &carry, bool &head,
+                                            uint64_t &acc, uint32_t &acc_list, uint32_t *status) {
+  const int s = lane >> 3, c = lane & 7;
+  uint32_t li = src.find(cx.u0);
+  bp_list L = src.get(li);
+  uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+  uint32_t kind = list_kind<MODE>(data, L);
+  if (MODE != kColsum && cx.u0 + cx.cnt <= nxt && (kind != kD4) != OTHER) return;
+  if (cx.staged == kChunk && (MODE == kColsum || (kind != kD4) == OTHER)) {
+    // Fast path: all 32 units are staged blocks of list li (no list change,
+    // no tail unit); each lane's block offset in the stage and width are
+    // packed into one word.
+    const uint64_t k0 = cx.u0 - L.unit_base;
+    if (k0 == 0) {
+      carry = 0;
+      head = true;
     }
-    uint32_t carry = 0;
-    if (MODE != kColsum) carry = comp(sc.chunk[ch], s);
-    bool head = false;
-    if (staged == kChunk) {
-      // Fast path: all 32 units are staged blocks of list li (no list change,
-      // no tail unit); each lane's block offset in the stage and width are
-      // packed into one word.
-      const uint64_t k0 = u0 - L.unit_base;
-      if (k0 == 0) {
-        carry = 0;
-        head = true;
-      }
-      const uint32_t pk = (uint32_t)((eL & kOffMask) - st0) | (uint32_t)((eL >> 56) << 16);
-      if (MODE == kSum && acc_list != li) {
-        if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
-        acc_list = li;
-      }
-      uint32_t *o = MODE == kStore ? out + L.out_offset + 128ull * k0 + 16 * c + s : nullptr;
-      if constexpr (MODE == kColsum || !OTHER) {
-        staged_chunk<MODE, kD4>(pk, sbase, lane, carry, o, acc);
-      } else {
-        if (kind == kDM) staged_chunk<MODE, kDM>(pk, sbase, lane, carry, o, acc);
-        else if (kind == kD2) staged_chunk<MODE, kD2>(pk, sbase, lane, carry, o, acc);
-        else staged_chunk<MODE, kD1>(pk, sbase, lane, carry, o, acc);
-      }
-      __syncwarp();  // every lane is done with the stage before it is refilled
-      if (MODE == kColsum) {
-        carry += __shfl_xor_sync(kFull, carry, 1);
-        carry += __shfl_xor_sync(kFull, carry, 2);
-        carry += __shfl_xor_sync(kFull, carry, 4);
-        const uint32_t c1 = __shfl_sync(kFull, carry, 8), c2 = __shfl_sync(kFull, carry, 16),
-                       c3 = __shfl_sync(kFull, carry, 24);
-        if (lane == 0) {
-          sc.chunk[ch] = make_uint4(carry, c1, c2, c3);
-          sc.chunk_head[ch] = head ? 1u : 0u;
-        }
+    const uint32_t pk = (uint32_t)((cx.eL & kOffMask) - cx.st0) | (uint32_t)((cx.eL >> 56) << 16);
+    if (MODE == kSum && acc_list != li) {
+      if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
+      acc_list = li;
+    }
+    uint32_t *o = MODE == kStore ? out + L.out_offset + 128ull * k0 + 16 * c + s : nullptr;
+    if constexpr (MODE == kColsum || !OTHER) {
+      staged_chunk<MODE, kD4>(pk, sbase, lane, carry, o, acc);
+    } else {
+      if (kind == kDM) staged_chunk<MODE, kDM>(pk, sbase, lane, carry, o, acc);
+      else if (kind == kD2) staged_chunk<MODE, kD2>(pk, sbase, lane, carry, o, acc);
+      else staged_chunk<MODE, kD1>(pk, sbase, lane, carry, o, acc);
+    }
+    return;
+  }
+  for (uint32_t j = 0; j < cx.cnt; j++) {
+    const uint64_t u = cx.u0 + j;
+    if (u == nxt) {
+      li++;
+      L = src.get(li);
+      nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+      kind = list_kind<MODE>(data, L);
+    }
+    const uint64_t k = u - L.unit_base;
+    if (k == 0) {
+      carry = 0;
+      head = true;
+    }
+    if (MODE != kColsum && (kind != kD4) != OTHER) continue;  // the other instance's list
+    const uint64_t e = __shfl_sync(kFull, cx.eL, j);
+    if (k >= L.n / 128u) {  // the tail unit: record the last packed value
+      if (MODE != kColsum) {
+        const uint32_t lv = kind_last(kind, carry);
+        if (lane == 24) sc.lastval[li] = lv;
       }
       continue;
     }
-    for (uint32_t j = 0; j < cnt; j++) {
-      const uint64_t u = u0 + j;
-      if (u == nxt) {
-        li++;
-        L = src.get(li);
-        nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
-        kind = list_kind<MODE>(data, L);
-      }
-      const uint64_t k = u - L.unit_base;
-      if (k == 0) {
-        carry = 0;
-        head = true;
-      }
-      if (MODE != kColsum && (kind != kD4) != OTHER) continue;  // the other kernel's list
-      const uint64_t e = __shfl_sync(kFull, eL, j);
-      if (k >= L.n / 128u) {  // the tail unit: record the last packed value
-        if (MODE != kColsum) {
-          const uint32_t lv = kind_last(kind, carry);
-          if (lane == 24) sc.lastval[li] = lv;
-        }
-        continue;
-      }
-      const uint32_t b = (uint32_t)(e >> 56);
-      if (b > 32u) {
-        if (MODE == kColsum && lane == 0 && sc.list_qm[li] != 0u) set_status(status, BP_ERR_CORRUPT);
-        continue;
-      }
-      uint32_t d[4];
-      if (j < staged)
-        pl_block_deltas_from((int)b, PlSharedWords{sbase + (uint32_t)((e & kOffMask) - st0)}, lane, d);
-      else
-        pl_block_deltas((int)b, data + L.enc_offset + (e & kOffMask), lane, d);
-      if (MODE == kColsum) {
-        carry += d[0] + d[1] + d[2] + d[3];
-        continue;
-      }
-      uint32_t x0, x1, x2, x3;
-      if constexpr (!OTHER) {
-        x0 = d[0];
-        x1 = x0 + d[1];
-        x2 = x1 + d[2];
-        x3 = x2 + d[3];
-        uint32_t inc = x3;
-#pragma unroll
-        for (int dd = 1; dd < 8; dd <<= 1) {
-          const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
-          if (c >= dd) inc += t;
-        }
-        const uint32_t base = carry + inc - x3;
-        x0 += base;
-        x1 += base;
-        x2 += base;
-        x3 += base;
-        carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
-      } else {
-        uint32_t x[4], ctot;
-        if (kind == kDM) prefix_block<kDM>(d, kind_seed<kDM>(carry), lane, x, ctot);
-        else if (kind == kD2) prefix_block<kD2>(d, kind_seed<kD2>(carry), lane, x, ctot);
-        else prefix_block<kD1>(d, kind_seed<kD1>(carry), lane, x, ctot);
-        carry += ctot;
-        x0 = x[0];
-        x1 = x[1];
-        x2 = x[2];
-        x3 = x[3];
-      }
-      if (MODE == kSum) {
-        if (acc_list != li) {
-          if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
-          acc_list = li;
-        }
-        acc += (uint64_t)x0 + x1 + x2 + x3;
-      } else {
-        uint32_t *o = out + L.out_offset + 128ull * k + 16 * c + s;
-        o[0] = x0;
-        o[4] = x1;
-        o[8] = x2;
-        o[12] = x3;
-      }
+    const uint32_t b = (uint32_t)(e >> 56);
+    if (b > 32u) {
+      if (MODE == kColsum && !OTHER && lane == 0 && sc.list_qm[li] != 0u)
+        set_status(status, BP_ERR_CORRUPT);
+      continue;
     }
-    if (staged) __syncwarp();  // every lane is done with the stage before it is refilled
+    uint32_t d[4];
+    if (j < cx.staged)
+      pl_block_deltas_from((int)b, PlSharedWords{sbase + (uint32_t)((e & kOffMask) - cx.st0)}, lane, d);
+    else
+      pl_block_deltas((int)b, data + L.enc_offset + (e & kOffMask), lane, d);
     if (MODE == kColsum) {
-      carry += __shfl_xor_sync(kFull, carry, 1);
-      carry += __shfl_xor_sync(kFull, carry, 2);
-      carry += __shfl_xor_sync(kFull, carry, 4);
-      const uint32_t c1 = __shfl_sync(kFull, carry, 8), c2 = __shfl_sync(kFull, carry, 16),
-                     c3 = __shfl_sync(kFull, carry, 24);
+      carry += d[0] + d[1] + d[2] + d[3];
+      continue;
+    }
+    uint32_t x0, x1, x2, x3;
+    if constexpr (!OTHER) {
+      x0 = d[0];
+      x1 = x0 + d[1];
+      x2 = x1 + d[2];
+      x3 = x2 + d[3];
+      uint32_t inc = x3;
+#pragma unroll
+      for (int dd = 1; dd < 8; dd <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+        if (c >= dd) inc += t;
+      }
+      const uint32_t bs = carry + inc - x3;
+      x0 += bs;
+      x1 += bs;
+      x2 += bs;
+      x3 += bs;
+      carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
+    } else {
+      uint32_t x[4], ctot;
+      if (kind == kDM) prefix_block<kDM>(d, kind_seed<kDM>(carry), lane, x, ctot);
+      else if (kind == kD2) prefix_block<kD2>(d, kind_seed<kD2>(carry), lane, x, ctot);
+      else prefix_block<kD1>(d, kind_seed<kD1>(carry), lane, x, ctot);
+      carry += ctot;
+      x0 = x[0];
+      x1 = x[1];
+      x2 = x[2];
+      x3 = x[3];
+    }
+    if (MODE == kSum) {
+      if (acc_list != li) {
+        if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
+        acc_list = li;
+      }
+      acc += (uint64_t)x0 + x1 + x2 + x3;
+    } else {
+      uint32_t *o = out + L.out_offset + 128ull * k + 16 * c + s;
+      o[0] = x0;
+      o[4] = x1;
+      o[8] = x2;
+      o[12] = x3;
+    }
+  }
+}
+
+// A tile is kTileChunks chunks of kChunk units, one per chunk warp, taken by
+// a CTA in ticket order (a tile only waits for tiles that running CTAs
+// hold).  The CTA has kTileChunks chunk warps and one control warp, and it
+// works on two tiles at once:
+//  - the chunk warps stage their chunk of tile i+1 in one of their two
+//    buffers and sum its columns (phase 1), while the control warp looks
+//    back for tile i's seed (the column sums of its first list over the
+//    earlier tiles) and hands each chunk warp its seed;
+//  - after a barrier the chunk warps decode their chunk of tile i from the
+//    other buffer (phase 2), while the control warp publishes tile i+1's
+//    sums and takes the next ticket.
+// So the look-back's latency overlaps phase 1, and the compressed stream
+// is read from memory once.  OTHER = false decodes the D4 lists, OTHER =
+// true the DM, D2 and D1 lists (launched after the first, leaving at once
+// if there are none); each runs its own tiles and look-back state.
+template <int MODE, bool OTHER>
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
+    pl_tiles(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
+             uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t spin_limit,
+             uint32_t *status) {
+  if (sc.ctl[0] || (OTHER && !sc.ctl[1])) return;
+  constexpr int kW = kTileChunks;  // chunk warps; warp kW is the control warp
+  __shared__ __align__(128) uint8_t s_stage[2][kW][kStageBytes];
+  __shared__ __align__(8) uint64_t s_bar[2][kW];
+  __shared__ uint4 s_sum[2][kW], s_seed[kW];
+  __shared__ uint32_t s_head[2][kW];
+  __shared__ uint64_t s_u0[2][kW], s_st0[2][kW];  // a chunk's first unit, stage offset
+  __shared__ uint32_t s_cnt[2][kW], s_staged[2][kW];
+  __shared__ unsigned long long s_tile[2];
+  __shared__ uint32_t s_abort;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool control = w == kW;
+  uint32_t parity = 0;  // bit b: phase parity of buffer b's mbarrier
+  if (!control && lane == 0) {
+    bulk_bar_init(smem_addr(&s_bar[0][w]));
+    bulk_bar_init(smem_addr(&s_bar[1][w]));
+  }
+  const uint64_t nch = (total_units + kChunk - 1) / kChunk;
+  const uint64_t ntiles = (nch + kW - 1) / kW;
+  const PlScratch st = OTHER ? sc_other(sc, ntiles) : sc;  // this instance's look-back state
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_tile[0] = atomicAdd(st.op_ticket, 1ull);
+  }
+  __syncthreads();
+  uint64_t acc = 0;
+  uint32_t acc_list = kNone;
+  bool pub_any = false;
+  for (int i = 0, first = 1;; i ^= 1, first = 0) {
+    // phase 1 of a chunk warp: stage chunk w of tile `t` in buffer b and sum
+    // its columns; the control warp then publishes the tile's sums
+    const int b = first ? 0 : i ^ 1;
+    const uint64_t t = first ? s_tile[0] : s_tile[i ^ 1];
+    uint64_t tile = 0;
+    if (!first) {
+      tile = s_tile[i];
+      if (tile >= ntiles || s_abort) break;
+    }
+    if (control) {
+      if (!first) {
+        // the seed of `tile`: its first list continues from earlier tiles
+        // unless the tile starts at a list head
+        uint4 agg = make_uint4(0, 0, 0, 0);
+        for (int k = 0; k < kW; k++) agg = s_head[i][k] ? s_sum[i][k] : add4(agg, s_sum[i][k]);
+        const uint64_t u0 = tile * kW * kChunk;
+        const bool starts = src.unit_base(src.find(u0)) == u0;
+        uint4 e = starts ? make_uint4(0, 0, 0, 0)
+                         : tile_lookback(st, tile, spin_limit, status, lane);
+        if (!pub_any && lane == 0) tile_publish(st, tile, 2u, add4(e, agg));
+        if (lane == 0) {
+          for (int k = 0; k < kW; k++) {
+            s_seed[k] = e;
+            e = s_head[i][k] ? s_sum[i][k] : add4(e, s_sum[i][k]);
+          }
+        }
+      }
+    } else {
+      const uint64_t ch = t * kW + w;
+      bool ok = true, head = false;
+      uint32_t carry = 0;
+      if (t < ntiles && ch < nch) {
+        const uint32_t sb = smem_addr(&s_stage[b][w][0]);
+        Chunk cx;
+        uint32_t ph = (parity >> b) & 1u;
+        ok = stage_chunk(data, src, sc, ch, total_units, lane, smem_addr(&s_bar[b][w]), sb, ph,
+                         cx, status);
+        parity = (parity & ~(1u << b)) | (ph << b);
+        if (lane == 0) {
+          s_u0[b][w] = cx.u0;
+          s_cnt[b][w] = cx.cnt;
+          s_staged[b][w] = cx.staged;
+          s_st0[b][w] = cx.st0;
+        }
+        if (ok)
+          chunk_units<kColsum, OTHER>(data, src, sc, cx, out, sums, sb, lane, carry, head, acc,
+                                      acc_list, status);
+        carry += __shfl_xor_sync(kFull, carry, 1);
+        carry += __shfl_xor_sync(kFull, carry, 2);
+        carry += __shfl_xor_sync(kFull, carry, 4);
+      }
+      const uint4 cs = make_uint4(__shfl_sync(kFull, carry, 0), __shfl_sync(kFull, carry, 8),
+                                  __shfl_sync(kFull, carry, 16), __shfl_sync(kFull, carry, 24));
       if (lane == 0) {
-        sc.chunk[ch] = make_uint4(carry, c1, c2, c3);
-        sc.chunk_head[ch] = head ? 1u : 0u;
+        s_sum[b][w] = cs;
+        s_head[b][w] = (ch >= nch || head) ? 1u : 0u;  // past the end: nothing continues
+        if (!ok) s_abort = 1;
       }
     }
+    __syncthreads();
+    if (s_abort) break;
+    if (control) {
+      if (t < ntiles) {  // publish t's sums, take the ticket after it
+        uint4 agg = make_uint4(0, 0, 0, 0);
+        bool any = false;
+        for (int k = 0; k < kW; k++) {
+          agg = s_head[b][k] ? s_sum[b][k] : add4(agg, s_sum[b][k]);
+          any |= s_head[b][k] != 0u;
+        }
+        if (lane == 0) tile_publish(st, t, any ? 2u : 1u, agg);
+        pub_any = any;
+      }
+      if (lane == 0) s_tile[first ? 1 : i] = t < ntiles ? atomicAdd(st.op_ticket, 1ull) : t;
+    } else if (!first && tile * kW + w < nch) {
+      // phase 2: decode chunk w of `tile` from buffer i with its seed
+      Chunk cx;
+      cx.u0 = s_u0[i][w];
+      cx.cnt = s_cnt[i][w];
+      cx.staged = s_staged[i][w];
+      cx.st0 = s_st0[i][w];
+      cx.eL = (uint32_t)lane < cx.cnt ? sc.boffw[cx.u0 + lane] : kBadEntry;
+      uint32_t carry = comp(s_seed[w], lane >> 3);
+      bool head = false;
+      chunk_units<MODE, OTHER>(data, src, sc, cx, out, sums, smem_addr(&s_stage[i][w][0]), lane,
+                               carry, head, acc, acc_list, status);
+      __syncwarp();  // every lane is done with buffer i before it is refilled
+    }
+    __syncthreads();
+    if (first) i = 1;  // after the first pass tile s_tile[0] sits in buffer 0: i becomes 0
   }
   if (MODE == kSum && acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
 }
-
-// ---- segmented exclusive scan of the chunk sums ---------------------------------------------
-
-struct SegV {
-  uint4 v;
-  uint32_t h;  // a list starts inside: the sum restarts there
-};
-
-__device__ __forceinline__ uint4 add4(const uint4 &a, const uint4 &b) {
-  return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-
-__device__ __forceinline__ SegV seg_op(const SegV &a, const SegV &b) {
-  SegV r;
-  r.v = b.h ? b.v : add4(a.v, b.v);
-  r.h = a.h | b.h;
-  return r;
-}
-
-__device__ __forceinline__ SegV seg_zero() {
-  SegV r;
-  r.v = make_uint4(0, 0, 0, 0);
-  r.h = 0;
-  return r;
-}
-
-__device__ __forceinline__ SegV seg_shfl_up(const SegV &a, int d) {
-  SegV r;
-  r.v.x = __shfl_up_sync(kFull, a.v.x, d);
-  r.v.y = __shfl_up_sync(kFull, a.v.y, d);
-  r.v.z = __shfl_up_sync(kFull, a.v.z, d);
-  r.v.w = __shfl_up_sync(kFull, a.v.w, d);
-  r.h = __shfl_up_sync(kFull, a.h, d);
-  return r;
-}
-
-// CTA-wide exclusive segmented scan; `total` receives the CTA's aggregate.
-template <int NT>
-__device__ __forceinline__ SegV cta_excl_scan(const SegV &x, SegV &total) {
-  __shared__ SegV s_w[NT / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  SegV inc = x;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const SegV y = seg_shfl_up(inc, d);
-    if (lane >= d) inc = seg_op(y, inc);
-  }
-  SegV ex = seg_shfl_up(inc, 1);
-  if (lane == 0) ex = seg_zero();
-  if (lane == 31) s_w[w] = inc;
-  __syncthreads();
-  SegV pre = seg_zero(), tot = seg_zero();
-  for (int i = 0; i < NT / 32; i++) {
-    if (i == w) pre = tot;
-    tot = seg_op(tot, s_w[i]);
-  }
-  total = tot;
-  __syncthreads();
-  return seg_op(pre, ex);
-}
-
-__device__ __forceinline__ SegV chunk_val(const PlScratch &sc, uint64_t i) {
-  SegV r;
-  r.v = sc.chunk[i];
-  r.h = sc.chunk_head[i];
-  return r;
-}
-
-__global__ void __launch_bounds__(kThreads) pl_scan_reduce(uint64_t nch, PlScratch sc) {
-  if (sc.ctl[0]) return;
-  const uint64_t t = blockIdx.x, base = t * kScanTile + (uint64_t)threadIdx.x * kScanPer;
-  SegV a = seg_zero();
-  for (uint32_t i = 0; i < kScanPer; i++)
-    if (base + i < nch) a = seg_op(a, chunk_val(sc, base + i));
-  SegV tot;
-  cta_excl_scan<kThreads>(a, tot);
-  if (threadIdx.x == 0) {
-    sc.tile[t] = tot.v;
-    sc.tile_head[t] = tot.h;
-  }
-}
-
-__global__ void __launch_bounds__(1024) pl_scan_top(uint64_t ntiles, PlScratch sc) {
-  if (sc.ctl[0]) return;
-  SegV carry = seg_zero();
-  for (uint64_t base = 0; base < ntiles; base += 1024) {
-    const uint64_t i = base + threadIdx.x;
-    SegV x = seg_zero();
-    if (i < ntiles) {
-      x.v = sc.tile[i];
-      x.h = sc.tile_head[i];
-    }
-    SegV tot;
-    const SegV ex = cta_excl_scan<1024>(x, tot);
-    if (i < ntiles) sc.tile[i] = seg_op(carry, ex).v;
-    carry = seg_op(carry, tot);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) pl_scan_down(uint64_t nch, PlScratch sc) {
-  if (sc.ctl[0]) return;
-  const uint64_t t = blockIdx.x, base = t * kScanTile + (uint64_t)threadIdx.x * kScanPer;
-  SegV a[kScanPer];
-  SegV agg = seg_zero();
-#pragma unroll
-  for (uint32_t i = 0; i < kScanPer; i++) {
-    a[i] = base + i < nch ? chunk_val(sc, base + i) : seg_zero();
-    agg = seg_op(agg, a[i]);
-  }
-  SegV tot, r;
-  const SegV ex = cta_excl_scan<kThreads>(agg, tot);
-  r.v = sc.tile[t];
-  r.h = 0;
-  r = seg_op(r, ex);
-#pragma unroll
-  for (uint32_t i = 0; i < kScanPer; i++) {
-    if (base + i < nch) sc.chunk[base + i] = r.v;
-    r = seg_op(r, a[i]);
-  }
-}
-
-// ---- varint tail -----------------------------------------------------------------------------
 
 template <bool SUM>
 __global__ void __launch_bounds__(kThreads)
@@ -1087,10 +1164,10 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <class K>
-int resident_grid(K kernel, int &per_sm_cache) {
+int resident_grid(K kernel, int threads, int &per_sm_cache) {
   if (per_sm_cache < 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess ||
         nb < 1)
       nb = 1;
     per_sm_cache = nb;
@@ -1114,39 +1191,42 @@ int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
   const PlLayout L = pl_layout(total_units, src.count);
   const PlScratch sc = carve(scratch, L);
   const uint64_t nch = (total_units + kChunk - 1) / kChunk;
-  const uint64_t ntiles = (nch + kScanTile - 1) / kScanTile;
+  const uint64_t ntl = (nch + kTileChunks - 1) / kTileChunks;
   const int sms = device_sm_count();
-  static int occ_col = -1, occ_store = -1, occ_sum = -1;
-  const uint64_t want_warps = nch;
-  auto unit_grid = [&](int resident) {
-    return (int)std::max<uint64_t>(
-        1, std::min<uint64_t>((want_warps + kThreads / 32 - 1) / (kThreads / 32), resident));
-  };
   const int lgrid = (int)std::min<uint64_t>((src.count + 7) / 8, 4096);
+  uint32_t spin_limit = 0, withhold = 0;
+  lookback_limits(spin_limit, withhold);
   if (cudaMemsetAsync(sc.boffw, 0xFF, 8 * total_units, s) != cudaSuccess) return BP_ERR_CUDA;
+  // tickets and look-back flags of both pl_tiles instances
+  const size_t op_clear = (size_t)(reinterpret_cast<uint8_t *>(sc.op_flag) -
+                                   reinterpret_cast<uint8_t *>(sc.op_ticket)) + 8 * ntl;
+  if (cudaMemsetAsync(sc.op_ticket, 0, op_clear, s) != cudaSuccess) return BP_ERR_CUDA;
   pl_plan<<<1, 1024, 0, s>>>(data, src, total_units, S, G, sc, status);
   pl_parse<<<8 * sms, kThreads, 0, s>>>(data, src, sc);
   pl_resolve<<<(int)std::min<uint64_t>(src.count, 4ull * sms), kThreads, 0, s>>>(data, src, sc,
                                                                                    status);
   pl_emit<<<8 * sms, kThreads, 0, s>>>(data, src, sc, status);
   pl_leftover<<<lgrid, kThreads, 0, s>>>(data, src, sc, out_cap, sums != nullptr, status);
-  pl_units<kColsum><<<unit_grid(resident_grid(pl_units<kColsum>, occ_col)), kThreads, 0, s>>>(
-      data, src, total_units, out, sums, sc, status);
-  pl_scan_reduce<<<(unsigned)ntiles, kThreads, 0, s>>>(nch, sc);
-  pl_scan_top<<<1, 1024, 0, s>>>(ntiles, sc);
-  pl_scan_down<<<(unsigned)ntiles, kThreads, 0, s>>>(nch, sc);
-  static int occ_sum_k = -1, occ_store_k = -1;
+  // persistent grids of resident CTAs; tiles are taken in ticket order
+  static int occ[4] = {-1, -1, -1, -1};
+  auto grid = [&](int resident) {
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(ntl, (uint64_t)resident));
+  };
   if (sums) {
-    pl_units<kSum><<<unit_grid(resident_grid(pl_units<kSum>, occ_sum)), kThreads, 0, s>>>(
-        data, src, total_units, out, sums, sc, status);
-    pl_units<kSum, true><<<unit_grid(resident_grid(pl_units<kSum, true>, occ_sum_k)), kThreads,
-                           0, s>>>(data, src, total_units, out, sums, sc, status);
+    pl_tiles<kSum, false><<<grid(resident_grid(pl_tiles<kSum, false>, kTileThreads, occ[0])),
+                            kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc, spin_limit,
+                                              status);
+    pl_tiles<kSum, true><<<grid(resident_grid(pl_tiles<kSum, true>, kTileThreads, occ[1])),
+                           kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc, spin_limit,
+                                             status);
     pl_tail<true><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   } else {
-    pl_units<kStore><<<unit_grid(resident_grid(pl_units<kStore>, occ_store)), kThreads, 0, s>>>(
-        data, src, total_units, out, sums, sc, status);
-    pl_units<kStore, true><<<unit_grid(resident_grid(pl_units<kStore, true>, occ_store_k)),
-                             kThreads, 0, s>>>(data, src, total_units, out, sums, sc, status);
+    pl_tiles<kStore, false><<<grid(resident_grid(pl_tiles<kStore, false>, kTileThreads, occ[2])),
+                              kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc,
+                                                spin_limit, status);
+    pl_tiles<kStore, true><<<grid(resident_grid(pl_tiles<kStore, true>, kTileThreads, occ[3])),
+                             kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc, spin_limit,
+                                               status);
     pl_tail<false><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   }
   return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
