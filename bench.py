@@ -67,6 +67,11 @@ def parse_args():
                    help="with --queries-only: index and batch this many times smaller")
     p.add_argument("--profile-queries", type=int, default=0,
                    help="with --profile-case queries: only the first N queries of the batch")
+    p.add_argument("--profile-tuning", default="",
+                   help="with --profile-case queries: dense_blocks,query_chunk_blocks,"
+                        "query_warps,merge_span to install first (the autotuner's choice)")
+    p.add_argument("--serving-only", action="store_true",
+                   help="only the serving measurements on the batched-query index")
     p.add_argument("--serving-sweep", action="store_true",
                    help="only the serving engine at 1M queries/s offered over slot counts "
                         "and batch sizes")
@@ -230,6 +235,76 @@ def profiled_traffic(sha: str):
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
     return float(m_b.group(1))
+
+
+# source files of each kernel with a counted instruction cost (profiles/issue_counts.md)
+KERNEL_SOURCES = {
+    "gl_decode": ["common.cuh", "bulk.cuh", "gl_block.cuh", "decode_gl.cu", "format.h", "decode.h"],
+    "gl_decode_sum": ["common.cuh", "bulk.cuh", "gl_block.cuh", "decode_gl.cu", "format.h",
+                      "decode.h"],
+    "gp_decode": ["common.cuh", "bulk.cuh", "gl_block.cuh", "decode_pfor.cu", "format.h",
+                  "decode.h"],
+    "fused_pair": ["common.cuh", "gl_block.cuh", "intersect.cuh", "lookback.cuh", "intersect.cu",
+                   "tuning.h"],
+    "q_main": ["common.cuh", "gl_block.cuh", "intersect.cuh", "lookback.cuh", "query.cu",
+               "tuning.h"],
+    "pl_tiles": ["common.cuh", "bulk.cuh", "gl_block.cuh", "pl_block.cuh", "decode_pl.cu",
+                 "format.h", "decode.h"],
+}
+
+
+def source_sha(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1401_6399_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def issue_counts() -> dict:
+    """Warp-instructions per unit of work from profiles/issue_counts.md, for
+    the kernels whose sources are unchanged since the capture."""
+    out = {}
+    try:
+        text = open(os.path.join(ROOT, "profiles", "issue_counts.md")).read()
+    except OSError:
+        return out
+    for m in re.finditer(r"^\| (\w+) \| ([^|]+) \| (\d+) \| (\d+) \| ([0-9.]+) \| (\w+) \| "
+                         r"([0-9a-f]+) \|$", text, flags=re.M):
+        key = m.group(1)
+        src = "q_main" if key.startswith("q_main") else key  # q_main_t<tuning>
+        if src in KERNEL_SOURCES and source_sha(KERNEL_SOURCES[src]) == m.group(7):
+            out[key] = {"case": m.group(2).strip(), "per_unit": float(m.group(5)),
+                        "unit": m.group(6)}
+    return out
+
+
+def issue_roof(key: str, units: float, ms: float, sm_mhz) -> dict | None:
+    """Issue roofline of one launch: counted warp-instructions (per unit x
+    units) over its time, against SMs x 4 schedulers x 1 warp-instruction
+    per cycle at the sampled SM clock."""
+    e = issue_counts().get(key)
+    if e is None or not ms or not sm_mhz:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    inst = e["per_unit"] * units
+    achieved = inst / (ms * 1e-3) / 1e9
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_instructions_per_launch": int(inst),
+            "per_unit": f"{e['per_unit']} per {e['unit']} (ncu smsp__inst_executed.sum, "
+                        f"{e['case']}; profiles/issue_counts.md)",
+            "clock_mhz": sm_mhz}
+
+
+def load_sm_max():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return 2070.0
 
 
 def load_peaks():
@@ -433,7 +508,7 @@ def unpack_sweep(stream, reps: int = 20, lists: int = 12, n: int = 1 << 20):
     return {"widths": "0..32", "ints_per_launch": total, "gints": res}
 
 
-def pair_sweep(stream, reps: int, cpu_threads: int = 0):
+def pair_sweep(stream, reps: int, cpu_threads: int = 0, sm_mhz=None):
     """Longer list 2^22 uniform values of [0,2^26); shorter lists of 2^22 .. 2^8
     values sharing 10% of theirs; fused vs unfused bp_intersect_pair, L2
     flushed before every call (one pair fits in L2).  cpu_threads > 0: the
@@ -515,6 +590,9 @@ def pair_sweep(stream, reps: int, cpu_threads: int = 0):
         row["fused_alg_bytes"] = alg
         row["fused_gbs"] = round(alg / (row["fused_us"] * 1e-6) / 1e9, 1)
         row["candidate_blocks"] = int(cand.size)
+        if m == f.size:  # the counted launch: m = n = 2^22
+            row["roofline"] = issue_roof("fused_pair", 1, row["fused_us"] * 1e-3,
+                                         sm_mhz or load_sm_max())
         if cpu_threads:
             row.update(cpu_pair_rates(encr, encf, k, cpu_threads))
             row["gpu_vs_cpu_1t"] = round(row["cpu_us_1t"] / row["fused_us"], 1)
@@ -604,16 +682,19 @@ def pair_batch(stream, reps: int, pairs: int = 64):
     return out
 
 
-def graph_batch(idx, terms, toff, total, stream, reps):
+def graph_batch(idx, terms, toff, total, stream, reps, out_pinned: bool = False):
     """bp_query_batch over idx captured in a CUDA graph and replayed `reps`
-    times; returns (ms per batch, answers, offsets, counts)."""
+    times; returns (ms per batch, answers, offsets, counts).  out_pinned:
+    the answers go to pinned host memory (written by the kernels over the
+    host link, as the serving engine delivers them) instead of HBM."""
     import torch
     from paper_1401_6399_gb300 import capi
     nq = toff.size - 1
     dev = "cuda"
     d_terms = torch.from_numpy(terms.view(np.int32).copy()).to(dev)
     d_off = torch.from_numpy(toff.view(np.int64).copy()).to(dev)
-    out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    out = (torch.empty(max(total, 1), dtype=torch.int32).pin_memory() if out_pinned else
+           torch.empty(max(total, 1), dtype=torch.int32, device=dev))
     out_off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     counts = torch.empty(nq, dtype=torch.int32, device=dev)
     sb = capi.bp_query_batch_scratch_bytes(idx.h_lists, terms, toff, total)
@@ -675,7 +756,7 @@ def query_alg_bytes(idx, vals, offs, terms, toff, sample: int, seed: int) -> flo
 
 
 def batched_queries(stream, reps: int, plain_queries: int, scale: int = 1,
-                    hybrid_bs=(8, 16, 32), cpu_threads: int = 0):
+                    hybrid_bs=(8, 16, 32), cpu_threads: int = 0, sm_mhz=None):
     """Synthetic index of 2^19 terms over [0,2^25), Zipf(1) lengths capped at
     2^24 (1.5e9 postings, clustered lists, GL with skip headers, resident);
     100,000 queries of 2-5 terms drawn in proportion to list length.  One
@@ -779,7 +860,11 @@ def batched_queries(stream, reps: int, plain_queries: int, scale: int = 1,
                          "100 on one thread): every term's GL stream decoded by the scalar "
                          "oracle, then Set-vs-Set by merging",
                "gpu_vs_cpu": round(qps / qps_c, 1)}
-    return {"queries": nq, "cpu_baseline": cpu, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
+    # counted for one tuning: reported when the autotuner chose the same
+    tkey = "q_main_t{dense_blocks}_{query_chunk_blocks}_{query_warps}_{merge_span}".format(
+        **tuned["best"])
+    roof = (issue_roof(tkey, nq, ms, sm_mhz or load_sm_max()) if scale == 1 else None)
+    return {"queries": nq, "cpu_baseline": cpu, "roofline": roof, "ms_per_batch": round(ms, 3), "queries_per_s": round(qps, 1),
             "plain_queries_timed": qn, "plain_queries_per_s": round(qps_plain, 1),
             "speedup_vs_plain": round(qps / qps_plain, 1), "answer_values": total,
             "index_postings": int(lens.sum()), "index_bytes": idx.compressed_bytes,
@@ -906,9 +991,16 @@ def serving(idx, lens, rates=(1e4, 1e5, 1e6)):
     ms, res, _, _ = graph_batch(idx, terms, toff, int(o[-1]), stream, 3)
     del res
     torch.cuda.empty_cache()
+    # the same batch with its answers written to pinned host memory, as the
+    # engine delivers them: the host link's share of the saturation rate
+    ms_h, res, _, _ = graph_batch(idx, terms, toff, int(o[-1]), stream, 3, out_pinned=True)
+    del res
     out["offline_same_mix"] = {"queries": nq, "ms_per_batch": round(ms, 3),
                                "queries_per_s": round(nq / (ms * 1e-3), 1),
-                               "answer_values": int(o[-1])}
+                               "answer_values": int(o[-1]),
+                               "answers_to_host_queries_per_s": round(nq / (ms_h * 1e-3), 1),
+                               "answers_to_host_gbs": round(4 * int(o[-1]) / (ms_h * 1e-3) / 1e9,
+                                                            1)}
     return out
 
 
@@ -1042,15 +1134,22 @@ def run_ours(args, rank, world, local):
                      "frac_of_nominal_8TBs": round(achieved / 8000.0, 4)},
     }
 
+    if layout == capi.BP_LAYOUT_GPU:
+        result["roofline_issue"] = issue_roof("gl_decode", total_n / 128, ms_local,
+                                              clk["sm_mhz"] or load_sm_max())
+
     extra = {}
     if not args.no_extra:
         reps = max(5, min(50, args.steps // 4))
+        sm_mhz = clk["sm_mhz"] or load_sm_max()
         # decode + sum (compressed bytes only)
         sums = torch.zeros(L, dtype=torch.int64, device="cuda")
         ms_sum = time_launches(stream, lambda: batch.sum_into(sums, status, stream), reps, 2)
         extra[f"{lay_name}_decode_sum_uniform"] = {
             "gints": round(total_n / (ms_sum * 1e-3) / 1e9, 2), "ms": round(ms_sum, 4),
-            "gbs_compressed": round(comp_bytes / (ms_sum * 1e-3) / 1e9, 1)}
+            "gbs_compressed": round(comp_bytes / (ms_sum * 1e-3) / 1e9, 1),
+            "roofline": (issue_roof("gl_decode_sum", total_n / 128, ms_sum, sm_mhz)
+                         if lay_name == "gl" else None)}
         # clustered lists
         cl = make_lists("clustered", L, n, UNIVERSE, seed + 1000)
         cbatch = api.ListBatch(encode_all(cl, capi.BP_LAYOUT_GPU), [n] * L, capi.BP_LAYOUT_GPU)
@@ -1083,7 +1182,12 @@ def run_ours(args, rank, world, local):
                 pfor[f"{dname}_{kname}"] = {
                     "gints": round(total_n / (ms_g * 1e-3) / 1e9, 2), "ms": round(ms_g, 4),
                     "bits_per_int": round(8 * gb.compressed_bytes / total_n, 3),
-                    "gl_bits_per_int": round(8 * gl_bytes / total_n, 3)}
+                    "gl_bits_per_int": round(8 * gl_bytes / total_n, 3),
+                    "hbm_gbs": round((gb.compressed_bytes + 4 * total_n) / (ms_g * 1e-3) / 1e9,
+                                     1)}
+                if dname == "uniform" and kname == "D4":
+                    pfor[f"{dname}_{kname}"]["roofline"] = issue_roof(
+                        "gp_decode", total_n / 128, ms_g, sm_mhz)
                 del gb
             del want
         extra["gp_decode_s4fastpfor"] = pfor
@@ -1130,7 +1234,7 @@ def run_ours(args, rank, world, local):
             extra["unpack_sweep"] = {"error": repr(e)[:300]}
         cpu_t = 0 if (args.no_cpu or world > 1 or rank != 0) else min(16, os.cpu_count() or 1)
         try:
-            extra["pair_sweep"] = pair_sweep(stream, reps=20, cpu_threads=cpu_t)
+            extra["pair_sweep"] = pair_sweep(stream, reps=20, cpu_threads=cpu_t, sm_mhz=sm_mhz)
         except Exception as e:  # report, do not hide the headline
             extra["pair_sweep"] = {"error": repr(e)[:300]}
         try:
@@ -1140,7 +1244,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
         try:
             extra["batched_queries"] = batched_queries(stream, reps=5, plain_queries=2000,
-                                                       cpu_threads=cpu_t)
+                                                       cpu_threads=cpu_t, sm_mhz=sm_mhz)
         except Exception as e:
             extra["batched_queries"] = {"error": repr(e)[:300]}
         try:
@@ -1243,6 +1347,10 @@ def profile_case(args) -> dict:
         lens = W.zipf_lengths((1 << 19) // sc, 1_500_000_000 // sc, (1 << 24) // sc)
         vals, offs = W.many("clustered", lens, 0, 1 << 25, 0x4000)
         idx = api.Index(vals, offs)
+        if args.profile_tuning:
+            d, c, wp, mg = (int(x) for x in args.profile_tuning.split(","))
+            capi.bp_set_tuning(dense_blocks=d, query_chunk_blocks=c, query_warps=wp,
+                               merge_span=mg)
         terms, toff = W.queries(lens, 100_000 // sc, W.CLUEWEB_TERM_WEIGHTS_2_5, 2, 0x4A00)
         if args.profile_queries:  # a sample: the first N queries of the batch
             nq = min(args.profile_queries, toff.size - 1)
@@ -1251,6 +1359,7 @@ def profile_case(args) -> dict:
         stream = torch.cuda.Stream()
         ms, _, _, _ = graph_batch(idx, terms, toff, int(o[-1]), stream, args.steps)
         return {"profile_case": "queries", "scale": sc, "queries": int(toff.size - 1),
+                "tuning": capi.bp_get_tuning(),
                 "ms": round(ms, 4), "queries_per_s": round((toff.size - 1) / (ms * 1e-3), 1)}
     n, L = 1 << args.log2n, 4
     lists = make_lists("uniform", L, n, UNIVERSE, SEED_BASE)
@@ -1287,6 +1396,14 @@ def main():
         print(json.dumps({"pair_sweep": pair_sweep(stream, reps=args.steps),
                           "pair_batch_64": pair_batch(stream, reps=max(3, args.steps))}),
               flush=True)
+        return
+    if args.serving_only:
+        import torch
+        import __graft_entry__ as ge
+        ge.build()
+        stream = torch.cuda.Stream()
+        batched_queries(stream, reps=2, plain_queries=10, hybrid_bs=())
+        print(json.dumps({"serving": serving(*batched_queries.index)}), flush=True)
         return
     if args.serving_sweep:
         import torch

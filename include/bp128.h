@@ -417,9 +417,12 @@ int bp_query_one(const uint8_t *d_data, const bp_list *h_lists,
  * order as long as their scratch and answer capacity fit the slot's memory,
  * and launches them with bp_query_batch on the slot's stream, so new
  * requests join while earlier batches are still on the GPU and several
- * batches overlap on the device.  Answers are written by the kernels into
- * the slot's pinned host memory, which must be device-accessible (pinned
- * memory on a unified-address system).  The engine allocates no device or
+ * batches overlap on the device.  The kernels write a batch's answers to
+ * the slot's device memory (slot_bytes holds them and the batch's scratch)
+ * and its answer counts and offsets to the slot's pinned host memory, which
+ * must be device-accessible (pinned memory on a unified-address system);
+ * once the batch is done the engine copies exactly its answer values to the
+ * pinned memory with one transfer.  The engine allocates no device or
  * pinned memory and creates only one event per slot. */
 typedef struct bp_server bp_server;
 

@@ -1052,7 +1052,20 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
       const uint64_t ch = t * kW + w;
       bool ok = true, head = false;
       uint32_t carry = 0;
+      // a chunk inside one list of the other instance's kind: nothing to sum
+      // or decode here, and no chunk of this kind looks back past it (a
+      // look-back stays within one list), so it counts as a list head
+      bool mine = true;
       if (t < ntiles && ch < nch) {
+        const uint64_t u0 = ch * kChunk;
+        const uint32_t li = src.find(u0);
+        const uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
+        const uint64_t end = u0 + kChunk < total_units ? u0 + kChunk : total_units;
+        const bp_list L = src.get(li);
+        const uint32_t k = L.enc_bytes >= 16 ? rd_u32(data + L.enc_offset + 12) : 0u;
+        mine = !(end <= nxt && ((k <= 3u ? k : 0u) != kD4) != OTHER);
+      }
+      if (t < ntiles && ch < nch && mine) {
         const uint32_t sb = smem_addr(&s_stage[b][w][0]);
         Chunk cx;
         uint32_t ph = (parity >> b) & 1u;
@@ -1075,8 +1088,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
       const uint4 cs = make_uint4(__shfl_sync(kFull, carry, 0), __shfl_sync(kFull, carry, 8),
                                   __shfl_sync(kFull, carry, 16), __shfl_sync(kFull, carry, 24));
       if (lane == 0) {
+        if (!(t < ntiles && ch < nch && mine)) s_cnt[b][w] = 0u;  // no phase 2
         s_sum[b][w] = cs;
-        s_head[b][w] = (ch >= nch || head) ? 1u : 0u;  // past the end: nothing continues
+        s_head[b][w] = (ch >= nch || head || !mine) ? 1u : 0u;  // past the end: nothing continues
         if (!ok) s_abort = 1;
       }
     }
@@ -1094,7 +1108,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         pub_any = any;
       }
       if (lane == 0) s_tile[first ? 1 : i] = t < ntiles ? atomicAdd(st.op_ticket, 1ull) : t;
-    } else if (!first && tile * kW + w < nch) {
+    } else if (!first && tile * kW + w < nch && s_cnt[i][w] != 0u) {
       // phase 2: decode chunk w of `tile` from buffer i with its seed
       Chunk cx;
       cx.u0 = s_u0[i][w];

@@ -5,9 +5,15 @@
 // CUDA streams, one device buffer and one pinned host buffer.  Each slot
 // owns a fixed slice of both.  Queries are submitted from any host thread
 // and wait in an arrival queue.  A dispatcher thread repeatedly
-//   - retires slots whose batch has finished (one event per batch; the
-//     kernels wrote answers, counts and offsets straight into the slot's
-//     pinned host memory), stamping each query's completion time, and
+//   - moves on slots whose batch has finished on the device: the kernels
+//     wrote the answers to the slot's device memory and the counts and
+//     offsets straight into its pinned host memory, so the exact number of
+//     answer values is known and one copy-engine transfer brings them to
+//     the slot's pinned memory (kernel stores over the host link measured
+//     58 GB/s, half what this needs at the device's query rate; the copy
+//     engines move about 190 GB/s);
+//   - retires slots whose transfer has finished, stamping each query's
+//     completion time, and
 //   - admits waiting queries into every free slot, in arrival order, as long
 //     as the batch's scratch and answer capacity fit the slot's memory, and
 //     launches bp_query_batch for them on the slot's stream.
@@ -65,6 +71,7 @@ struct Slot {
   cudaStream_t stream;
   cudaEvent_t ev;
   bool busy = false;
+  bool copying = false;  // the answers are on their way to pinned memory
   // device slice
   uint8_t *d_base;
   uint32_t *d_terms;
@@ -169,7 +176,8 @@ bool bp_server::admit(Slot &s, uint32_t slot_index) {
     const uint64_t cap2 = cap + nmin, items2 = items + qitems;
     const size_t need = bp::query_batch_scratch_for(terms.size() + p.k, (uint32_t)take.size() + 1,
                                                     std::max<uint64_t>(cap2, 1), items2);
-    const bool fits_dev = need <= slot_dev - fixed_dev;
+    const bool fits_dev =  // answers, then scratch
+        need + up256(4 * std::max<uint64_t>(cap2, 1)) <= slot_dev - fixed_dev;
     const bool fits_host = 4 * cap2 <= slot_host - fixed_host;
     if (!fits_dev || !fits_host) {
       if (take.empty()) {  // can never fit this slot: reject it
@@ -208,11 +216,15 @@ bool bp_server::admit(Slot &s, uint32_t slot_index) {
            cudaSuccess ||
        cudaMemsetAsync(s.d_status, 0, 4, st) != cudaSuccess))
     rc = BP_ERR_CUDA;
+  // the answers go to the front of the slot's device memory, the scratch
+  // after them; counts and offsets straight to pinned memory
   const uint64_t out_cap = std::max<uint64_t>(cap, 1);
+  const size_t ans_bytes = up256(4 * out_cap);
   if (rc == BP_OK)
     rc = bp::launch_query_batch(d_data, d_lists, n_terms, s.d_terms, s.d_toff, terms.size(), nq,
-                                s.h_answers, out_cap, s.h_out_off, s.h_counts, s.d_scratch,
-                                slot_dev - fixed_dev, s.d_status, st);
+                                reinterpret_cast<uint32_t *>(s.d_scratch), out_cap, s.h_out_off,
+                                s.h_counts, s.d_scratch + ans_bytes,
+                                slot_dev - fixed_dev - ans_bytes, s.d_status, st);
   if (rc == BP_OK &&
       (cudaMemcpyAsync(s.h_status, s.d_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
        cudaEventRecord(s.ev, st) != cudaSuccess))
@@ -253,8 +265,9 @@ void bp_server::retire(Slot &s) {
     out.push_back(std::move(d));
   }
   s.rec.answer_values = values;
-  s.rec.done_s = t;
+  if (s.rec.done_s == 0.0) s.rec.done_s = t;
   s.rec.retired_s = now_s();
+  s.copying = false;
   {
     std::lock_guard<std::mutex> g(mu);
     for (auto &d : out) done.push_back(std::move(d));
@@ -271,11 +284,24 @@ void bp_server::run() {
   cudaSetDevice(device);
   while (true) {
     bool worked = false;
-    for (auto &s : slots)
-      if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) {
-        retire(s);
-        worked = true;
+    for (auto &s : slots) {
+      if (!s.busy || cudaEventQuery(s.ev) != cudaSuccess) continue;
+      worked = true;
+      if (!s.copying) {  // the batch is done on the device: bring its answers over
+        s.rec.done_s = now_s();
+        const uint64_t total = s.h_out_off[s.batch.size()];
+        if ((int)*s.h_status == BP_OK && total > 0 && total <= s.out_cap) {
+          if (cudaMemcpyAsync(s.h_answers, s.d_scratch, 4 * total, cudaMemcpyDeviceToHost,
+                              s.stream) == cudaSuccess &&
+              cudaEventRecord(s.ev, s.stream) == cudaSuccess) {
+            s.copying = true;
+            continue;
+          }
+          *s.h_status = BP_ERR_CUDA;
+        }
       }
+      retire(s);
+    }
     take_arrivals();
     for (uint32_t i = 0; i < slots.size(); i++)
       if (!slots[i].busy && admit(slots[i], i)) worked = true;
