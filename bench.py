@@ -465,12 +465,12 @@ def gl_widths(enc: np.ndarray) -> np.ndarray:
 
 
 def unpack_sweep(stream, reps: int = 20, lists: int = 12, n: int = 1 << 20):
-    """Unpacking speed per bit width (Section 7.4, Fig. 4) on the GPU: for
+    """Unpacking speed per bit width (Section 7.4, Figure 6) on the GPU: for
     b = 0..32 and each kind, `lists` GL lists of n integers whose blocks all
     have width b (stepped walks modulo 2^32, BP_ENCODE_ANY_ORDER), decoded
     by one bp_decode_batch (the product kernels) and by bp_decode_ablation
     with the prefix integrated (one pass) or applied as a separate pass over
-    a block buffer in shared memory (two pass, Fig. 4a).  12 x 2^20 integers: 48 MiB out plus at most
+    a block buffer in shared memory (two pass, Figure 6a).  12 x 2^20 integers: 48 MiB out plus at most
     48 MiB in, so repeated launches run from L2 and time the unpacking, not
     HBM.  Gint/s, CUDA events over `reps` launches captured in one CUDA
     graph."""

@@ -272,7 +272,7 @@ int bp_decode_batch(const uint8_t *d_data, const bp_list *d_lists,
 /* Decode GPU-layout lists of any kind with the differential coding either
  * integrated into the unpacking (two_pass = 0: each unpacked 4-vector is
  * prefixed before it is stored, Algorithm 1) or applied as a separate pass
- * (two_pass = 1, the regular scheme Section 7.4 measures against, Fig. 4a):
+ * (two_pass = 1, the regular scheme Section 7.4 measures against, Figure 6a):
  * each block's deltas are stored to a buffer of 128 words of shared memory
  * per warp, read back and prefixed.  Both variants run one list-major
  * kernel of identical structure, so the difference between them is what

@@ -1,7 +1,7 @@
 // decode_ablation.cu -- GL decoding with the differential coding integrated
 // into the unpacking or applied as a separate pass (bp_decode_ablation).
 //
-// Section 7.4 (Fig. 4a) compares the integrated unpacking of Algorithm 1
+// Section 7.4 (Figure 6a) compares the integrated unpacking of Algorithm 1
 // (the prefix of Section 5 applied to each unpacked 4-vector before it is
 // stored) with the regular scheme, in which a block is first unpacked to
 // memory and the prefix then runs over it as a second pass.  Both variants
