@@ -1137,6 +1137,14 @@ def run_ours(args, rank, world, local):
     if layout == capi.BP_LAYOUT_GPU:
         result["roofline_issue"] = issue_roof("gl_decode", total_n / 128, ms_local,
                                               clk["sm_mhz"] or load_sm_max())
+        # context for the HBM fraction: the decode is write-dominated (1.9 GB in,
+        # 8.6 GB out) while the measured peak is a half-read, half-write copy;
+        # a pure write of the same output (torch's fill of 8 GiB) on this GPU
+        def fill():
+            with torch.cuda.stream(stream):  # on the stream the events are recorded on
+                out.fill_(0)
+        ms_fill = time_launches(stream, fill, 5, 2)
+        result["roofline"]["write_only_fill_gbs"] = round(4 * total_n / (ms_fill * 1e-3) / 1e9, 1)
 
     extra = {}
     if not args.no_extra:
