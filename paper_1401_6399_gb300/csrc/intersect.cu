@@ -41,8 +41,11 @@ constexpr int kPairWarpWords = kPairGroups * 128 + kIxDenseMax * 128 + kPairGrou
 // whose value range covers at most merge_span blocks of f per block of r
 // (similar densities) is merged with those blocks of f (merge_run_hits);
 // otherwise the warp filters it 128 values at a time with its window of f
-// moving forward (dense) or by per-value probes (sparse).  merge_span = 0
-// turns the merge regime off.
+// moving forward (dense) or by per-value probes (sparse).  MERGE: the
+// instance with the merge regime, launched when the tuning's merge_span is
+// not 0 (the out-of-line merge call alone costs the kernel instructions
+// where it is not taken).
+template <bool MERGE>
 __global__ void __launch_bounds__(kIxThreads, 3)
     fused_pair_kernel(PairArgs a, Compaction cp, TileOut to, uint32_t ntiles, uint32_t dense_max,
                       uint32_t vpw, uint32_t merge_span) {
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(kIxThreads, 3)
     }
     __syncwarp();
     bool merged = false;
-    if (merge_span != 0u && na > 0u && F.nblocks > 0u) {
+    if (MERGE && merge_span != 0u && na > 0u && F.nblocks > 0u) {
       const int64_t kl = warp_ubound(F.first, F.nblocks, s_r[na - 1], lane);
       if (kl < 0) {  // the whole run is below f's first value
         alive = 0;
@@ -230,15 +233,20 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
   if (mode == BP_MODE_FUSED) {
     int dev = 0, per_sm = 1;  // resident CTAs of fused_pair_kernel per SM
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BP_ERR_CUDA;
+    auto *const kern = tu.merge_span ? fused_pair_kernel<true> : fused_pair_kernel<false>;
     {
       std::lock_guard<std::mutex> g(g_pair_mu);
       if (!((g_pair_smem_set >> dev) & 1u)) {
-        if (cudaFuncSetAttribute(fused_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(fused_pair_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kPairSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(fused_pair_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kPairSmem) != cudaSuccess)
           return BP_ERR_CUDA;
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_pair_kernel, kIxThreads,
-                                                          kPairSmem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_pair_kernel<false>,
+                                                          kIxThreads, kPairSmem) != cudaSuccess ||
             n < 1)
           n = 1;
         g_pair_per_sm[dev] = n;
@@ -249,8 +257,9 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
     const uint32_t vpw = pair_vpw(a.nr, a.nf, (uint64_t)per_sm * device_sm_count());
     const uint32_t ft = pair_tiles(a.nr, vpw);
     if (cudaMemsetAsync(sp, 0, compaction_bytes(ft), s) != cudaSuccess) return BP_ERR_CUDA;
-    fused_pair_kernel<<<ft, kIxThreads, kPairSmem, s>>>(
-        a, cp, to, ft, std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw, tu.merge_span);
+    kern<<<ft, kIxThreads, kPairSmem, s>>>(a, cp, to, ft,
+                                           std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw,
+                                           tu.merge_span);
     return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
   }
   // unfused: decode both lists into scratch, then intersect the arrays
