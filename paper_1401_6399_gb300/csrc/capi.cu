@@ -59,7 +59,7 @@ int decode_common(const uint8_t *d_enc, size_t enc_bytes, int layout, size_t n, 
 // they are forked from the caller's stream by an event and joined back into
 // it, so the call keeps the order of the work on that stream.
 
-constexpr int kPipeGroups = 8;
+constexpr int kPipeGroups = 32;  // small groups: the first copy-in (before any copy-out) is short
 constexpr int kNotPipelined = -1;
 
 struct HostPipe {
