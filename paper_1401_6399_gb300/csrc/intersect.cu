@@ -32,9 +32,13 @@ struct PairArgs {
 };
 
 // Shared memory per warp: up to 8 decoded blocks of r (survivors compacted
-// in place), the window of f, and one hit bit per value of r (merge regime).
+// in place), the window of f, and in the merge instance one hit bit per
+// value of r (kept out of the other instance, whose 3 CTAs per SM then stay
+// within the smaller shared-memory carveout).
 constexpr int kPairGroups = 8;
-constexpr int kPairWarpWords = kPairGroups * 128 + kIxDenseMax * 128 + kPairGroups * 4;
+constexpr int pair_warp_words(bool merge) {
+  return kPairGroups * 128 + kIxDenseMax * 128 + (merge ? kPairGroups * 4 : 0);
+}
 
 // vpw: values of the shorter list per warp: a power of two 8..128 (a slice
 // of one block, for very skewed pairs) or 128 g for g = 1..8 blocks.  A run
@@ -55,9 +59,9 @@ __global__ void __launch_bounds__(kIxThreads, 3)
   __syncthreads();
   const uint32_t t = s_tile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t *s_r = smem + w * kPairWarpWords;
+  uint32_t *s_r = smem + w * pair_warp_words(MERGE);
   uint32_t *s_f = s_r + kPairGroups * 128;
-  uint32_t *s_hit = s_f + kIxDenseMax * 128;
+  uint32_t *s_hit = s_f + kIxDenseMax * 128;  // MERGE only
 
   GlView R, F;
   bool okR = gl_view(a.r_enc, a.r_bytes, R) && R.n == a.nr;
@@ -201,7 +205,7 @@ uint32_t pair_vpw(uint64_t nr, uint64_t nf, uint64_t resident) {
 std::mutex g_pair_mu;
 uint64_t g_pair_smem_set = 0;
 int g_pair_per_sm[64];
-constexpr size_t kPairSmem = sizeof(uint32_t) * kPairWarpWords * kIxWarps;
+constexpr size_t pair_smem(bool merge) { return sizeof(uint32_t) * pair_warp_words(merge) * kIxWarps; }
 
 }  // namespace
 
@@ -239,14 +243,15 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
       if (!((g_pair_smem_set >> dev) & 1u)) {
         if (cudaFuncSetAttribute(fused_pair_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kPairSmem) != cudaSuccess ||
+                                 (int)pair_smem(false)) != cudaSuccess ||
             cudaFuncSetAttribute(fused_pair_kernel<true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kPairSmem) != cudaSuccess)
+                                 (int)pair_smem(true)) != cudaSuccess)
           return BP_ERR_CUDA;
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_pair_kernel<false>,
-                                                          kIxThreads, kPairSmem) != cudaSuccess ||
+                                                          kIxThreads, pair_smem(false)) !=
+                cudaSuccess ||
             n < 1)
           n = 1;
         g_pair_per_sm[dev] = n;
@@ -257,7 +262,7 @@ int launch_intersect_pair(const uint8_t *da, size_t a_bytes, size_t na, const ui
     const uint32_t vpw = pair_vpw(a.nr, a.nf, (uint64_t)per_sm * device_sm_count());
     const uint32_t ft = pair_tiles(a.nr, vpw);
     if (cudaMemsetAsync(sp, 0, compaction_bytes(ft), s) != cudaSuccess) return BP_ERR_CUDA;
-    kern<<<ft, kIxThreads, kPairSmem, s>>>(a, cp, to, ft,
+    kern<<<ft, kIxThreads, pair_smem(tu.merge_span != 0u), s>>>(a, cp, to, ft,
                                            std::min<uint32_t>(tu.dense_blocks, kIxDenseMax), vpw,
                                            tu.merge_span);
     return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;

@@ -34,8 +34,11 @@ namespace {
 constexpr int kMaxTerms = 64;
 constexpr int kMaxChunk = 8;
 // per warp: the item's decoded blocks (survivors are compacted in place),
-// the dense window of the list being searched, one hit bit per candidate
-constexpr int kWarpSmemWords = kMaxChunk * 128 + kIxDenseMax * 128 + kMaxChunk * 4;
+// the dense window of the list being searched, and in the merge instance one
+// hit bit per candidate (kept out of the other instance: 1 KiB more per CTA
+// crossed a shared-memory carveout step and cost L1 space, 4 % of queries/s)
+constexpr int kWarpSmemBase = kMaxChunk * 128 + kIxDenseMax * 128;
+constexpr int warp_smem_words(bool merge) { return kWarpSmemBase + (merge ? kMaxChunk * 4 : 0); }
 
 inline size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -335,9 +338,9 @@ __global__ void __launch_bounds__(256, 3)
   if ((sc.counters[2] != 0ull) != HYB) return;
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t *s_r = smem + w * kWarpSmemWords;
+  uint32_t *s_r = smem + w * warp_smem_words(MERGE);
   uint32_t *s_f = s_r + kMaxChunk * 128;
-  uint32_t *s_hit = s_f + kIxDenseMax * 128;
+  uint32_t *s_hit = s_f + kIxDenseMax * 128;  // MERGE only
   const uint32_t total = sc.base[nq];
   if (total > max_items) {  // the caller's scratch holds fewer work items
     if (threadIdx.x == 0 && blockIdx.x == 0) set_status(status, BP_ERR_SCRATCH);
@@ -606,28 +609,29 @@ int launch_query_batch(const uint8_t *data, const bp_list *lists, uint32_t n_ter
   if (cudaMemsetAsync(sc.counters, 0, 256, s) != cudaSuccess) return BP_ERR_CUDA;
   if (nq == 0) return BP_OK;
   const int threads = 32 * (int)warps;
-  const size_t smem = sizeof(uint32_t) * kWarpSmemWords * warps;
+  const bool mrg = tu.merge_span != 0u;
+  const size_t smem = sizeof(uint32_t) * warp_smem_words(mrg) * warps;
   {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BP_ERR_CUDA;
     std::lock_guard<std::mutex> g(g_main_mu);
     if (!((g_main_smem_set >> dev) & 1u)) {
-      const int bytes = (int)(sizeof(uint32_t) * kWarpSmemWords * 8);
+      const int plain = (int)(sizeof(uint32_t) * warp_smem_words(false) * 8);
+      const int merge = (int)(sizeof(uint32_t) * warp_smem_words(true) * 8);
       if (cudaFuncSetAttribute(q_main_kernel<false, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, plain) != cudaSuccess ||
           cudaFuncSetAttribute(q_main_kernel<true, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, plain) != cudaSuccess ||
           cudaFuncSetAttribute(q_main_kernel<false, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, merge) != cudaSuccess ||
           cudaFuncSetAttribute(q_main_kernel<true, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, merge) != cudaSuccess)
         return BP_ERR_CUDA;
       g_main_smem_set |= 1ull << dev;
     }
   }
   // the instances for this tuning: compressed-only and hybrid, with or
   // without the merge regime
-  const bool mrg = tu.merge_span != 0u;
   auto *const kc = mrg ? q_main_kernel<false, true> : q_main_kernel<false, false>;
   auto *const kh = mrg ? q_main_kernel<true, true> : q_main_kernel<true, false>;
   int per_sm = 0, per_sm_h = 0;
