@@ -83,7 +83,7 @@ struct PlScratch {
   uint32_t *seg_base;   // [count + 1] first segment of each list; [count]: total
   uint32_t *grp_base;   // [count + 1] first group of each list; [count]: total
   uint32_t *ctl;        // [0] nonzero: the lists do not tile the units, do nothing;
-                        // [1] nonzero: some list is not D4
+                        // [1] nonzero: some list is not D4; [2] nonzero: some list is D4
   uint32_t *seg_in;     // [segs][kEnt] chain state entering the segment, by group entry
   uint32_t *live;       // [segs][kLiveCap] live line | successor distance << 16
   uint32_t *live_cnt;   // [segs]
@@ -208,12 +208,13 @@ __global__ void __launch_bounds__(1024)
             uint64_t max_g, PlScratch sc, uint32_t *status) {
   __shared__ uint64_t s_w[32][3];
   __shared__ uint64_t s_carry[3];
-  __shared__ uint32_t s_bad, s_other;
+  __shared__ uint32_t s_bad, s_other, s_d4;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) {
     s_carry[0] = s_carry[1] = s_carry[2] = 0;
     s_bad = 0;
     s_other = 0;
+    s_d4 = 0;
   }
   __syncthreads();
   for (uint64_t base = 0; base < src.count; base += 1024) {
@@ -248,6 +249,8 @@ __global__ void __launch_bounds__(1024)
       // those kinds have work
       if (L.enc_bytes >= 16 && (L.enc_offset & 15u) == 0 && rd_u32(data + L.enc_offset + 12) != 0u)
         s_other = 1;
+      else
+        s_d4 = 1;  // D4, or a bad header that the D4 passes report
       sc.seg_base[i] = (uint32_t)ex[1];
       sc.grp_base[i] = (uint32_t)ex[2];
     }
@@ -266,6 +269,7 @@ __global__ void __launch_bounds__(1024)
     sc.grp_base[src.count] = bad ? 0u : (uint32_t)s_carry[2];
     sc.ctl[0] = bad ? 1u : 0u;
     sc.ctl[1] = s_other;
+    sc.ctl[2] = s_d4;
     if (bad) set_status(status, BP_ERR_ARG);
   }
 }
@@ -992,7 +996,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
     pl_tiles(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
              uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t spin_limit,
              uint32_t *status) {
-  if (sc.ctl[0] || (OTHER && !sc.ctl[1])) return;
+  if (sc.ctl[0] || (OTHER ? !sc.ctl[1] : !sc.ctl[2])) return;  // no list of this kind
   constexpr int kW = kTileChunks;  // chunk warps; warp kW is the control warp
   __shared__ __align__(128) uint8_t s_stage[2][kW][kStageBytes];
   __shared__ __align__(8) uint64_t s_bar[2][kW];
