@@ -246,11 +246,23 @@ __device__ __forceinline__ void gl_block_values(int b, const uint32_t *__restric
 // few dozen instructions instead of 33 specialised routines -- for kernels
 // whose instruction footprint matters more than the last shift (the
 // intersections decode blocks at several call sites).  Lane l's value j
-// sits at bit 4bl + jb of the block's words w[0..4b).
+// sits at bit 4bl + jb of the block's words w[0..4b).  Up to b = 8 the
+// lane's 4b bits are read as one 32-bit window (one or two loads); wider
+// blocks read each field's word pair.
 __device__ __forceinline__ void gl_block_values_rt(uint32_t b, const uint32_t *__restrict__ w,
                                                    uint32_t F, int lane, uint32_t x[4]) {
   uint32_t d[4] = {0u, 0u, 0u, 0u};
-  if (b != 0u) {
+  if (b != 0u && b <= 8u) {
+    // the lane's 4b <= 32 bits lie in one 32-bit window of the stream: one
+    // or two loads and one funnel shift, then the four fields
+    const uint32_t p = 4u * b * (uint32_t)lane, k = p >> 5, o = p & 31u;
+    const uint32_t lo = __ldg(w + k);
+    const uint32_t hi = (o + 4u * b > 32u) ? __ldg(w + k + 1) : 0u;  // still in the lane's bits
+    const uint32_t u = __funnelshift_r(lo, hi, o);
+    const uint32_t mask = (1u << b) - 1u;
+#pragma unroll
+    for (int j = 0; j < 4; j++) d[j] = (u >> (b * (uint32_t)j)) & mask;
+  } else if (b != 0u) {
     const uint32_t mask = b >= 32u ? 0xFFFFFFFFu : (1u << b) - 1u;
     uint32_t bit = 4u * b * (uint32_t)lane;
 #pragma unroll
