@@ -19,17 +19,18 @@
 //          from its entry and records the byte offset and width of each block.
 //  rest    pl_leftover reads the fewer than 16 blocks after the meta-blocks
 //          (one width byte each) and checks the stream's size.
-//  decode  pl_onepass takes chunks of kOpC work units in ticket order.  A
-//          warp stages a chunk's blocks in shared memory with one bulk copy,
-//          unpacks each block once (Algorithm 1, 4-lane interleave) into a
-//          value buffer in shared memory, with running column sums that
-//          restart at every list head, and publishes the chunk's column sums.
-//          The seed of the chunk -- the column sums of its list's earlier
-//          blocks (Section 5) -- comes from a decoupled look-back over the
-//          chunks before it; the values are then stored with the seed added.
-//          So the compressed stream is read once here (and once by parse).
-//          pl_tail decodes the varint tail (Section 4.1) from the last packed
-//          value.
+//  decode  pl_tiles takes tiles of kTileChunks chunks of kChunk work units
+//          in ticket order, one chunk per warp.  A warp stages its chunk's
+//          blocks in shared memory with one bulk copy and sums their columns
+//          (one lane per block); the CTA publishes the tile's column sums,
+//          restarting at every list head.  The seed of a tile -- the column
+//          sums of its first list's earlier blocks (Section 5) -- comes from
+//          a decoupled look-back over the tiles before it, and the warps
+//          then unpack the staged blocks again (Algorithm 1, 4-lane
+//          interleave) and store them with the seed added.  So the
+//          compressed stream is read from memory once here (and once by
+//          parse).  pl_tail decodes the varint tail (Section 4.1) from the
+//          last packed value.
 //
 // Work unit u of a list: its block u - unit_base, then one unit for the tail.
 #include "decode.h"
@@ -52,7 +53,7 @@ constexpr uint32_t kChunk = 32;          // work units per warp and tile step
 constexpr int kTileChunks = 7;           // chunk warps per CTA of pl_tiles (+ a control warp)
 constexpr int kTileThreads = 32 * (kTileChunks + 1);
 constexpr int kTileMinBlocks = 4;        // resident CTAs per SM for pl_tiles
-constexpr uint32_t kStageBytes = 3840;   // per warp and buffer: 32 blocks of average width <= 7.5
+constexpr uint32_t kStageBytes = 3776;   // per warp and buffer: 32 blocks of average width <= 7.3
 constexpr uint64_t kOffMask = (1ull << 56) - 1;
 constexpr uint64_t kBadEntry = ~0ull;  // width byte 0xFF: no block to decode
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -646,15 +647,6 @@ __device__ __forceinline__ uint32_t kind_last(uint32_t kind, uint32_t carry) {
   return c3;  // D4 and DM: position 128 nb - 1 is in column 3
 }
 
-// Kind of differential coding of a list (header word 3; lists whose header
-// is bad are marked bad and never decoded).  The column sums need none.
-template <int MODE>
-__device__ __forceinline__ uint32_t list_kind(const uint8_t *data, const bp_list &L) {
-  if (MODE == kColsum || L.enc_bytes < 16) return kD4;
-  const uint32_t k = rd_u32(data + L.enc_offset + 12);
-  return k <= 3u ? k : kD4;
-}
-
 __device__ __forceinline__ uint32_t comp(const uint4 &v, int s) {
   return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
 }
@@ -799,6 +791,78 @@ __device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int la
 }
 
 
+// Column sums of a fully staged chunk, one lane per block.  Line k of a
+// block (16 bytes) holds word k of each of the 4 lane streams, and field i
+// of stream s is bits [b i, b i + b) of that stream (Section 4.2, Fig. 2):
+// lane j reads block j's lines in order through a window of three lines and
+// adds the 4 deltas of each field, one funnel shift each.  The width is a
+// run-time value: every lane runs the same 32 field steps.
+struct LbWin {
+  uint4 w0, w1, w2;  // lines kc, kc + 1 and kc + 2 (zeros past the block)
+  uint32_t kc;
+};
+
+__device__ __forceinline__ uint4 lb_line(const uint4 *lines, uint32_t k, uint32_t b) {
+  return k < b ? lines[k] : make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ uint4 lb_colsum(const uint4 *lines, uint32_t b) {
+  const uint32_t mask = b >= 32u ? ~0u : (1u << b) - 1u;
+  LbWin win{lb_line(lines, 0, b), lb_line(lines, 1, b), lb_line(lines, 2, b), 0};
+  uint4 sum = make_uint4(0, 0, 0, 0);
+  uint32_t p = 0;
+#pragma unroll 4
+  for (int i = 0; i < 32; i++, p += b) {
+    // field i starts at bit p: word k = p / 32 of each stream, joined with
+    // word k + 1 when it straddles; the window moves by at most one line
+    const uint32_t k = p >> 5, r = p & 31u;
+    if (k != win.kc) {
+      win.kc = k;
+      win.w0 = win.w1;
+      win.w1 = win.w2;
+      win.w2 = lb_line(lines, k + 2, b);
+    }
+    sum.x += __funnelshift_r(win.w0.x, win.w1.x, r) & mask;
+    sum.y += __funnelshift_r(win.w0.y, win.w1.y, r) & mask;
+    sum.z += __funnelshift_r(win.w0.z, win.w1.z, r) & mask;
+    sum.w += __funnelshift_r(win.w0.w, win.w1.w, r) & mask;
+  }
+  return sum;
+}
+
+// The list table as pl_tiles reads it: a copy in shared memory (with each
+// list's kind of deltas) when it has at most kListCache lists, so that
+// finding a chunk's list costs no global memory round trips.
+constexpr uint32_t kListCache = 32;
+
+struct TileLists {
+  ListSrc src;
+  const bp_list *sl;      // shared copy, or nullptr
+  const uint32_t *skind;  // shared kinds
+  uint32_t count;
+  __device__ __forceinline__ bp_list get(uint32_t i) const { return sl ? sl[i] : src.get(i); }
+  __device__ __forceinline__ uint64_t unit_base(uint32_t i) const {
+    return sl ? sl[i].unit_base : src.unit_base(i);
+  }
+  // list owning unit u: largest i with unit_base(i) <= u
+  __device__ __forceinline__ uint32_t find(uint64_t u) const {
+    uint32_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (unit_base(mid) <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
+  // kind of differential coding (header word 3; kD4 for a short or bad
+  // header, whose list is marked bad and never decoded)
+  __device__ __forceinline__ uint32_t kind(const uint8_t *data, uint32_t i, const bp_list &L) const {
+    if (sl) return skind[i];
+    const uint32_t k = L.enc_bytes >= 16 ? rd_u32(data + L.enc_offset + 12) : 0u;
+    return k <= 3u ? k : (uint32_t)kD4;
+  }
+};
+
 // A warp's chunk of kChunk work units and how much of it sits in the stage.
 struct Chunk {
   uint64_t u0;
@@ -812,7 +876,7 @@ struct Chunk {
 // in the meta-block region, 16-byte aligned, only width lines between them,
 // so one bulk copy brings them in when they fit.  False if the copy's wait
 // ran out (recorded; the copy has landed or given up when this returns).
-__device__ __forceinline__ bool stage_chunk(const uint8_t *data, const ListSrc &src,
+__device__ __forceinline__ bool stage_chunk(const uint8_t *data, const TileLists &src,
                                             const PlScratch &sc, uint64_t ch,
                                             uint64_t total_units, int lane, uint32_t bar,
                                             uint32_t sbase, uint32_t &phase, Chunk &cx,
@@ -853,32 +917,48 @@ __device__ __forceinline__ bool stage_chunk(const uint8_t *data, const ListSrc &
 
 // The chunk's units, once the stage is filled.  MODE kColsum: `carry` ends
 // as this lane's part of the column sums of the chunk's last list within the
-// chunk (from its head if it starts here: `head`).  MODE kStore / kSum: the
+// chunk (from its head if it starts here: `head`); a fully staged chunk sums
+// one block per lane and leaves all of column s in lane 8s.  MODE kStore / kSum: the
 // blocks of lists of this instance's kind (D4, or the others if OTHER) are
 // decoded with the running column sums `carry` (the chunk's seed on entry;
 // the same in the 8 lanes of a column), stored or summed; a list's tail unit
 // records its last packed value.
 template <int MODE, bool OTHER>
-__device__ __forceinline__ void chunk_units(const uint8_t *data, const ListSrc &src,
+__device__ __forceinline__ void chunk_units(const uint8_t *data, const TileLists &src,
                                             const PlScratch &sc, const Chunk &cx,
-                                            uint32_t *out, uint64_t *sums, uint32_t sbase,
+                                            uint32_t *out, uint64_t *sums, const uint4 *stage,
                                             int lane, uint32_t &carry, bool &head,
                                             uint64_t &acc, uint32_t &acc_list, uint32_t *status) {
   const int s = lane >> 3, c = lane & 7;
+  const uint32_t sbase = smem_addr(stage);
   uint32_t li = src.find(cx.u0);
   bp_list L = src.get(li);
   uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
-  uint32_t kind = list_kind<MODE>(data, L);
+  uint32_t kind = MODE == kColsum ? (uint32_t)kD4 : src.kind(data, li, L);
   if (MODE != kColsum && cx.u0 + cx.cnt <= nxt && (kind != kD4) != OTHER) return;
   if (cx.staged == kChunk && (MODE == kColsum || (kind != kD4) == OTHER)) {
     // Fast path: all 32 units are staged blocks of list li (no list change,
-    // no tail unit); each lane's block offset in the stage and width are
-    // packed into one word.
+    // no tail unit).
     const uint64_t k0 = cx.u0 - L.unit_base;
     if (k0 == 0) {
       carry = 0;
       head = true;
     }
+    if (MODE == kColsum) {
+      // one lane per block, then a sum over the lanes
+      const uint32_t ln = (uint32_t)(((cx.eL & kOffMask) - cx.st0) >> 4);
+      uint4 v = lb_colsum(stage + ln, (uint32_t)(cx.eL >> 56));
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        v.x += __shfl_xor_sync(kFull, v.x, d);
+        v.y += __shfl_xor_sync(kFull, v.y, d);
+        v.z += __shfl_xor_sync(kFull, v.z, d);
+        v.w += __shfl_xor_sync(kFull, v.w, d);
+      }
+      carry = c ? 0u : comp(v, s);
+      return;
+    }
+    // decode: each lane's block offset in the stage and width packed in one word
     const uint32_t pk = (uint32_t)((cx.eL & kOffMask) - cx.st0) | (uint32_t)((cx.eL >> 56) << 16);
     if (MODE == kSum && acc_list != li) {
       if (acc_list != kNone) flush_sum(acc, sums + acc_list, lane);
@@ -900,7 +980,7 @@ __device__ __forceinline__ void chunk_units(const uint8_t *data, const ListSrc &
       li++;
       L = src.get(li);
       nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
-      kind = list_kind<MODE>(data, L);
+      kind = MODE == kColsum ? (uint32_t)kD4 : src.kind(data, li, L);
     }
     const uint64_t k = u - L.unit_base;
     if (k == 0) {
@@ -993,12 +1073,14 @@ __device__ __forceinline__ void chunk_units(const uint8_t *data, const ListSrc &
 // if there are none); each runs its own tiles and look-back state.
 template <int MODE, bool OTHER>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
-    pl_tiles(const uint8_t *__restrict__ data, ListSrc src, uint64_t total_units,
+    pl_tiles(const uint8_t *__restrict__ data, ListSrc src_in, uint64_t total_units,
              uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t spin_limit,
              uint32_t *status) {
   if (sc.ctl[0] || (OTHER ? !sc.ctl[1] : !sc.ctl[2])) return;  // no list of this kind
   constexpr int kW = kTileChunks;  // chunk warps; warp kW is the control warp
   __shared__ __align__(128) uint8_t s_stage[2][kW][kStageBytes];
+  __shared__ bp_list s_lists[kListCache];
+  __shared__ uint32_t s_kinds[kListCache];
   __shared__ __align__(8) uint64_t s_bar[2][kW];
   __shared__ uint4 s_sum[2][kW], s_seed[kW];
   __shared__ uint32_t s_head[2][kW];
@@ -1016,6 +1098,16 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
   const uint64_t nch = (total_units + kChunk - 1) / kChunk;
   const uint64_t ntiles = (nch + kW - 1) / kW;
   const PlScratch st = OTHER ? sc_other(sc, ntiles) : sc;  // this instance's look-back state
+  const bool cached = src_in.count <= kListCache;
+  if (cached) {
+    for (uint32_t k = threadIdx.x; k < src_in.count; k += kTileThreads) {
+      const bp_list L = src_in.get(k);
+      s_lists[k] = L;
+      const uint32_t kd = L.enc_bytes >= 16 ? rd_u32(data + L.enc_offset + 12) : 0u;
+      s_kinds[k] = kd <= 3u ? kd : (uint32_t)kD4;
+    }
+  }
+  const TileLists src{src_in, cached ? s_lists : nullptr, s_kinds, src_in.count};
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_tile[0] = atomicAdd(st.op_ticket, 1ull);
@@ -1066,8 +1158,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         const uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
         const uint64_t end = u0 + kChunk < total_units ? u0 + kChunk : total_units;
         const bp_list L = src.get(li);
-        const uint32_t k = L.enc_bytes >= 16 ? rd_u32(data + L.enc_offset + 12) : 0u;
-        mine = !(end <= nxt && ((k <= 3u ? k : 0u) != kD4) != OTHER);
+        mine = !(end <= nxt && (src.kind(data, li, L) != kD4) != OTHER);
       }
       if (t < ntiles && ch < nch && mine) {
         const uint32_t sb = smem_addr(&s_stage[b][w][0]);
@@ -1083,8 +1174,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
           s_st0[b][w] = cx.st0;
         }
         if (ok)
-          chunk_units<kColsum, OTHER>(data, src, sc, cx, out, sums, sb, lane, carry, head, acc,
-                                      acc_list, status);
+          chunk_units<kColsum, OTHER>(data, src, sc, cx, out, sums,
+                                      reinterpret_cast<const uint4 *>(&s_stage[b][w][0]), lane,
+                                      carry, head, acc, acc_list, status);
         carry += __shfl_xor_sync(kFull, carry, 1);
         carry += __shfl_xor_sync(kFull, carry, 2);
         carry += __shfl_xor_sync(kFull, carry, 4);
@@ -1122,8 +1214,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
       cx.eL = (uint32_t)lane < cx.cnt ? sc.boffw[cx.u0 + lane] : kBadEntry;
       uint32_t carry = comp(s_seed[w], lane >> 3);
       bool head = false;
-      chunk_units<MODE, OTHER>(data, src, sc, cx, out, sums, smem_addr(&s_stage[i][w][0]), lane,
-                               carry, head, acc, acc_list, status);
+      chunk_units<MODE, OTHER>(data, src, sc, cx, out, sums,
+                               reinterpret_cast<const uint4 *>(&s_stage[i][w][0]), lane, carry,
+                               head, acc, acc_list, status);
       __syncwarp();  // every lane is done with buffer i before it is refilled
     }
     __syncthreads();
