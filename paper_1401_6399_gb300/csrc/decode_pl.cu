@@ -806,10 +806,37 @@ __device__ __forceinline__ uint4 lb_line(const uint4 *lines, uint32_t k, uint32_
   return k < b ? lines[k] : make_uint4(0, 0, 0, 0);
 }
 
+// Sum of the 4 b-bit fields (b <= 8) at the bottom of v: fields 0 + 2 and
+// 1 + 3 are added in place (each sum fits in b + 1 <= 2b bits), then folded.
+__device__ __forceinline__ uint32_t lb_sum4(uint32_t v, uint32_t b, uint32_t m02, uint32_t low) {
+  const uint32_t t = (v & m02) + ((v >> b) & m02);
+  return (t & low) + (t >> (2u * b));
+}
+
 __device__ __forceinline__ uint4 lb_colsum(const uint4 *lines, uint32_t b) {
   const uint32_t mask = b >= 32u ? ~0u : (1u << b) - 1u;
   LbWin win{lb_line(lines, 0, b), lb_line(lines, 1, b), lb_line(lines, 2, b), 0};
   uint4 sum = make_uint4(0, 0, 0, 0);
+  if (b <= 8u) {
+    // 4 fields (4b <= 32 bits) per step, from one funnel shift per stream
+    const uint32_t m02 = mask | (mask << (2u * b)), low = (1u << (2u * b)) - 1u;
+    uint32_t p = 0;
+#pragma unroll 2
+    for (int i = 0; i < 8; i++, p += 4u * b) {
+      const uint32_t k = p >> 5, r = p & 31u;
+      if (k != win.kc) {
+        win.kc = k;
+        win.w0 = win.w1;
+        win.w1 = win.w2;
+        win.w2 = lb_line(lines, k + 2, b);
+      }
+      sum.x += lb_sum4(__funnelshift_r(win.w0.x, win.w1.x, r), b, m02, low);
+      sum.y += lb_sum4(__funnelshift_r(win.w0.y, win.w1.y, r), b, m02, low);
+      sum.z += lb_sum4(__funnelshift_r(win.w0.z, win.w1.z, r), b, m02, low);
+      sum.w += lb_sum4(__funnelshift_r(win.w0.w, win.w1.w, r), b, m02, low);
+    }
+    return sum;
+  }
   uint32_t p = 0;
 #pragma unroll 4
   for (int i = 0; i < 32; i++, p += b) {
