@@ -1245,6 +1245,27 @@ def run_ours(args, rank, world, local):
             "gints": round(total_n / (ms_p * 1e-3) / 1e9, 2), "ms": round(ms_p, 4),
             "bits_per_int": round(8 * pbatch.compressed_bytes / total_n, 3)}
         del pbatch
+        # sparser lists (about 9 bits/int): paper-layout chunks wider than
+        # the shared-memory stage, read from global memory after an L2 prefetch
+        sp = make_lists("uniform", 8, n, 1 << 31, SEED_BASE + 0x100)
+        sn = 8 * n
+        sout = out[:sn]
+        swant = torch.from_numpy(np.concatenate(sp).view(np.int32)).to("cuda")
+        sparse = {"lists": 8, "ints_per_list": n, "universe": "[0,2^31)"}
+        for lname, lay in (("paper", capi.BP_LAYOUT_PAPER), ("gpu", capi.BP_LAYOUT_GPU)):
+            sb = api.ListBatch(encode_all(sp, lay), [n] * 8, lay)
+            with torch.cuda.stream(stream):
+                sb.decode_into(sout, status, stream)
+            stream.synchronize()
+            assert int(status.item()) == 0
+            assert torch.equal(sout, swant)
+            ms_s = time_launches(stream, lambda: sb.decode_into(sout, status, stream),
+                                 max(3, reps // 5), 1)
+            sparse[lname] = {"gints": round(sn / (ms_s * 1e-3) / 1e9, 2), "ms": round(ms_s, 4),
+                             "bits_per_int": round(8 * sb.compressed_bytes / sn, 3)}
+            del sb
+        extra["decode_sparse_uniform"] = sparse
+        del sp, swant, sout
         # the other kinds of differential coding (Section 5), both layouts
         kinds = {}
         for kname, kind in (("DM", capi.BP_DELTA_DM), ("D2", capi.BP_DELTA_D2),

@@ -712,8 +712,22 @@ __device__ __forceinline__ uint4 tile_lookback(const PlScratch &sc, uint64_t t,
   return excl;
 }
 
-template <int B, int MODE, int KIND>
-__device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run, uint32_t sbase,
+// Where a full chunk's blocks are read from: the shared-memory stage, or
+// global memory for a chunk too wide for the stage (after one L2 prefetch);
+// `off` is a block's byte offset from the chunk's first block.
+struct StagedBlocks {
+  uint32_t sbase;
+  __device__ __forceinline__ PlSharedWords at(uint32_t off) const { return PlSharedWords{sbase + off}; }
+};
+struct GlobalBlocks {
+  const uint8_t *p;  // 16-byte aligned
+  __device__ __forceinline__ PlGlobalWords<true> at(uint32_t off) const {
+    return PlGlobalWords<true>{p + off};
+  }
+};
+
+template <int B, int MODE, int KIND, class BL>
+__device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run, const BL &blocks,
                                            int lane, uint32_t &carry, uint32_t *&o,
                                            uint64_t &acc) {
   const int c = lane & 7;
@@ -721,7 +735,7 @@ __device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run
   for (uint32_t r = 0; r < run; r++) {
     const uint32_t p = __shfl_sync(kFull, pk, j + r);
     uint32_t d[4];
-    pl_lane_deltas<B>(PlSharedWords{sbase + (p & 0xFFFFu)}, lane, d);
+    pl_lane_deltas<B>(blocks.at(p & 0xFFFFu), lane, d);
     if (MODE == kColsum) {
       carry += d[0] + d[1] + d[2] + d[3];
       continue;
@@ -762,10 +776,10 @@ __device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run
   }
 }
 
-// The 32 blocks of a fully staged chunk, one width dispatch per run of
-// consecutive blocks of equal width.
-template <int MODE, int KIND>
-__device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int lane,
+// The 32 blocks of a full chunk, one width dispatch per run of consecutive
+// blocks of equal width.
+template <int MODE, int KIND, class BL>
+__device__ __forceinline__ void staged_chunk(uint32_t pk, const BL &blocks, int lane,
                                              uint32_t &carry, uint32_t *o, uint64_t &acc) {
   const uint32_t bw = pk >> 16;
   for (uint32_t j = 0; j < kChunk;) {
@@ -775,7 +789,7 @@ __device__ __forceinline__ void staged_chunk(uint32_t pk, uint32_t sbase, int la
     switch (b) {
 #define BP_CASE(B)                                                      \
   case B:                                                               \
-    staged_run<B, MODE, KIND>(pk, j, run, sbase, lane, carry, o, acc);  \
+    staged_run<B, MODE, KIND>(pk, j, run, blocks, lane, carry, o, acc); \
     break;
       BP_CASE(0) BP_CASE(1) BP_CASE(2) BP_CASE(3) BP_CASE(4) BP_CASE(5) BP_CASE(6)
       BP_CASE(7) BP_CASE(8) BP_CASE(9) BP_CASE(10) BP_CASE(11) BP_CASE(12) BP_CASE(13)
@@ -897,6 +911,7 @@ struct Chunk {
   uint64_t eL;      // lane j < cnt: boffw of unit u0 + j
   uint32_t staged;  // leading units whose blocks are in the stage
   uint64_t st0;     // stream offset of the stage's first byte
+  bool gl;          // a full chunk too wide for the stage: its blocks are read from global
 };
 
 // Stage the chunk's leading blocks of its first list: they lie back to back
@@ -913,6 +928,7 @@ __device__ __forceinline__ bool stage_chunk(const uint8_t *data, const TileLists
   cx.eL = (uint32_t)lane < cx.cnt ? sc.boffw[cx.u0 + lane] : kBadEntry;
   cx.staged = 0;
   cx.st0 = 0;
+  cx.gl = false;
   const uint32_t li = src.find(cx.u0);
   const bp_list L = src.get(li);
   const uint64_t nxt = li + 1 < src.count ? src.unit_base(li + 1) : ~0ull;
@@ -937,9 +953,29 @@ __device__ __forceinline__ bool stage_chunk(const uint8_t *data, const TileLists
       }
       cx.staged = (uint32_t)m;
       cx.st0 = st0;
+    } else if (bytes > 0 && m == kChunk) {
+      // too wide for the stage (average width above 7.3 bits): the fast
+      // paths read the blocks from global memory, pulled into L2 here
+      if (lane == 0) bulk_prefetch_l2(data + L.enc_offset + st0, (uint32_t)bytes);
+      cx.staged = kChunk;
+      cx.st0 = st0;
+      cx.gl = true;
     }
   }
   return true;
+}
+
+// Decode or sum a full chunk of this instance's kind.
+template <int MODE, bool OTHER, class BL>
+__device__ __forceinline__ void full_chunk(uint32_t kind, uint32_t pk, const BL &blocks, int lane,
+                                           uint32_t &carry, uint32_t *o, uint64_t &acc) {
+  if constexpr (MODE == kColsum || !OTHER) {
+    staged_chunk<MODE, kD4>(pk, blocks, lane, carry, o, acc);
+  } else {
+    if (kind == kDM) staged_chunk<MODE, kDM>(pk, blocks, lane, carry, o, acc);
+    else if (kind == kD2) staged_chunk<MODE, kD2>(pk, blocks, lane, carry, o, acc);
+    else staged_chunk<MODE, kD1>(pk, blocks, lane, carry, o, acc);
+  }
 }
 
 // The chunk's units, once the stage is filled.  MODE kColsum: `carry` ends
@@ -971,10 +1007,13 @@ __device__ __forceinline__ void chunk_units(const uint8_t *data, const TileLists
       carry = 0;
       head = true;
     }
+    const uint8_t *gblk = data + L.enc_offset + cx.st0;  // the chunk's first block in global
     if (MODE == kColsum) {
       // one lane per block, then a sum over the lanes
-      const uint32_t ln = (uint32_t)(((cx.eL & kOffMask) - cx.st0) >> 4);
-      uint4 v = lb_colsum(stage + ln, (uint32_t)(cx.eL >> 56));
+      const uint32_t off = (uint32_t)((cx.eL & kOffMask) - cx.st0);
+      const uint32_t b = (uint32_t)(cx.eL >> 56);
+      uint4 v = cx.gl ? lb_colsum(reinterpret_cast<const uint4 *>(gblk + off), b)
+                      : lb_colsum(stage + (off >> 4), b);
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         v.x += __shfl_xor_sync(kFull, v.x, d);
@@ -992,13 +1031,8 @@ __device__ __forceinline__ void chunk_units(const uint8_t *data, const TileLists
       acc_list = li;
     }
     uint32_t *o = MODE == kStore ? out + L.out_offset + 128ull * k0 + 16 * c + s : nullptr;
-    if constexpr (MODE == kColsum || !OTHER) {
-      staged_chunk<MODE, kD4>(pk, sbase, lane, carry, o, acc);
-    } else {
-      if (kind == kDM) staged_chunk<MODE, kDM>(pk, sbase, lane, carry, o, acc);
-      else if (kind == kD2) staged_chunk<MODE, kD2>(pk, sbase, lane, carry, o, acc);
-      else staged_chunk<MODE, kD1>(pk, sbase, lane, carry, o, acc);
-    }
+    if (cx.gl) full_chunk<MODE, OTHER>(kind, pk, GlobalBlocks{gblk}, lane, carry, o, acc);
+    else full_chunk<MODE, OTHER>(kind, pk, StagedBlocks{sbase}, lane, carry, o, acc);
     return;
   }
   for (uint32_t j = 0; j < cx.cnt; j++) {
@@ -1113,6 +1147,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
   __shared__ uint32_t s_head[2][kW];
   __shared__ uint64_t s_u0[2][kW], s_st0[2][kW];  // a chunk's first unit, stage offset
   __shared__ uint32_t s_cnt[2][kW], s_staged[2][kW];
+  __shared__ bool s_gl[2][kW];
   __shared__ unsigned long long s_tile[2];
   __shared__ uint32_t s_abort;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1199,6 +1234,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
           s_cnt[b][w] = cx.cnt;
           s_staged[b][w] = cx.staged;
           s_st0[b][w] = cx.st0;
+          s_gl[b][w] = cx.gl;
         }
         if (ok)
           chunk_units<kColsum, OTHER>(data, src, sc, cx, out, sums,
@@ -1238,6 +1274,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
       cx.cnt = s_cnt[i][w];
       cx.staged = s_staged[i][w];
       cx.st0 = s_st0[i][w];
+      cx.gl = s_gl[i][w];
       cx.eL = (uint32_t)lane < cx.cnt ? sc.boffw[cx.u0 + lane] : kBadEntry;
       uint32_t carry = comp(s_seed[w], lane >> 3);
       bool head = false;
