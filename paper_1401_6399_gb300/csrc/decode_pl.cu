@@ -33,6 +33,8 @@
 //          last packed value.
 //
 // Work unit u of a list: its block u - unit_base, then one unit for the tail.
+#include <type_traits>
+
 #include "decode.h"
 #include "bulk.cuh"
 #include "gl_block.cuh"
@@ -726,52 +728,81 @@ struct GlobalBlocks {
   }
 };
 
+// One block of a run: its deltas d become values, stored or summed, with
+// the running column sums `carry`.
+template <int MODE, int KIND>
+__device__ __forceinline__ void staged_block(uint32_t d[4], int lane, uint32_t &carry,
+                                             uint32_t *&o, uint64_t &acc) {
+  const int c = lane & 7;
+  if (MODE == kColsum) {
+    carry += d[0] + d[1] + d[2] + d[3];
+    return;
+  }
+  if constexpr (KIND != kD4) {
+    uint32_t x[4], ctot;
+    prefix_block<KIND>(d, kind_seed<KIND>(carry), lane, x, ctot);
+    carry += ctot;
+    if (MODE == kSum) {
+      acc += (uint64_t)x[0] + x[1] + x[2] + x[3];
+    } else {
+      o[0] = x[0];
+      o[4] = x[1];
+      o[8] = x[2];
+      o[12] = x[3];
+      o += 128;
+    }
+    return;
+  }
+  const uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
+  uint32_t inc = x3;
+#pragma unroll
+  for (int dd = 1; dd < 8; dd <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
+    if (c >= dd) inc += t;
+  }
+  const uint32_t base = carry + inc - x3;
+  carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
+  if (MODE == kSum) {
+    acc += (uint64_t)(x0 + base) + (x1 + base) + (x2 + base) + (x3 + base);
+  } else {
+    o[0] = x0 + base;
+    o[4] = x1 + base;
+    o[8] = x2 + base;
+    o[12] = x3 + base;
+    o += 128;
+  }
+}
+
 template <int B, int MODE, int KIND, class BL>
 __device__ __forceinline__ void staged_run(uint32_t pk, uint32_t j, uint32_t run, const BL &blocks,
                                            int lane, uint32_t &carry, uint32_t *&o,
                                            uint64_t &acc) {
-  const int c = lane & 7;
+  if constexpr (std::is_same<BL, GlobalBlocks>::value && KIND == kD4) {
+    // D4 blocks in global memory: the loads of two blocks are issued before
+    // either is used, so they share one round trip
+    uint32_t r = 0;
 #pragma unroll 1
-  for (uint32_t r = 0; r < run; r++) {
-    const uint32_t p = __shfl_sync(kFull, pk, j + r);
-    uint32_t d[4];
-    pl_lane_deltas<B>(blocks.at(p & 0xFFFFu), lane, d);
-    if (MODE == kColsum) {
-      carry += d[0] + d[1] + d[2] + d[3];
-      continue;
+    for (; r + 1 < run; r += 2) {
+      const uint32_t p0 = __shfl_sync(kFull, pk, j + r), p1 = __shfl_sync(kFull, pk, j + r + 1);
+      uint32_t d0[4], d1[4];
+      pl_lane_deltas<B>(blocks.at(p0 & 0xFFFFu), lane, d0);
+      pl_lane_deltas<B>(blocks.at(p1 & 0xFFFFu), lane, d1);
+      staged_block<MODE, KIND>(d0, lane, carry, o, acc);
+      staged_block<MODE, KIND>(d1, lane, carry, o, acc);
     }
-    if constexpr (KIND != kD4) {
-      uint32_t x[4], ctot;
-      prefix_block<KIND>(d, kind_seed<KIND>(carry), lane, x, ctot);
-      carry += ctot;
-      if (MODE == kSum) {
-        acc += (uint64_t)x[0] + x[1] + x[2] + x[3];
-      } else {
-        o[0] = x[0];
-        o[4] = x[1];
-        o[8] = x[2];
-        o[12] = x[3];
-        o += 128;
-      }
-      continue;
+    if (r < run) {
+      const uint32_t p0 = __shfl_sync(kFull, pk, j + r);
+      uint32_t d0[4];
+      pl_lane_deltas<B>(blocks.at(p0 & 0xFFFFu), lane, d0);
+      staged_block<MODE, KIND>(d0, lane, carry, o, acc);
     }
-    const uint32_t x0 = d[0], x1 = x0 + d[1], x2 = x1 + d[2], x3 = x2 + d[3];
-    uint32_t inc = x3;
-#pragma unroll
-    for (int dd = 1; dd < 8; dd <<= 1) {
-      const uint32_t t = __shfl_up_sync(kFull, inc, dd, 8);
-      if (c >= dd) inc += t;
-    }
-    const uint32_t base = carry + inc - x3;
-    carry += __shfl_sync(kFull, inc, (lane & ~7) | 7);
-    if (MODE == kSum) {
-      acc += (uint64_t)(x0 + base) + (x1 + base) + (x2 + base) + (x3 + base);
-    } else {
-      o[0] = x0 + base;
-      o[4] = x1 + base;
-      o[8] = x2 + base;
-      o[12] = x3 + base;
-      o += 128;
+  } else {
+#pragma unroll 1
+    for (uint32_t r = 0; r < run; r++) {
+      const uint32_t p = __shfl_sync(kFull, pk, j + r);
+      uint32_t d[4];
+      pl_lane_deltas<B>(blocks.at(p & 0xFFFFu), lane, d);
+      staged_block<MODE, KIND>(d, lane, carry, o, acc);
     }
   }
 }
