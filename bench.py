@@ -1241,9 +1241,15 @@ def run_ours(args, rank, world, local):
         assert torch.equal(out, torch.from_numpy(np.concatenate(lists).view(np.int32)).to("cuda"))
         ms_p = time_launches(stream, lambda: pbatch.decode_into(out, status, stream),
                              max(3, reps // 5), 1)
+        pl_gbs = (pbatch.compressed_bytes + 4 * total_n) / (ms_p * 1e-3) / 1e9
         extra["pl_decode_uniform"] = {
             "gints": round(total_n / (ms_p * 1e-3) / 1e9, 2), "ms": round(ms_p, 4),
-            "bits_per_int": round(8 * pbatch.compressed_bytes / total_n, 3)}
+            "bits_per_int": round(8 * pbatch.compressed_bytes / total_n, 3),
+            "roofline": {"bound": "hbm", "achieved": round(pl_gbs, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(pl_gbs / peak, 4),
+                         "scope": "the whole bp_decode_batch call (parse, offsets, decode); "
+                                  "algorithmic bytes = compressed + 4 B per integer, the "
+                                  "stream being read twice (parse and decode) not counted"}}
         del pbatch
         # sparser lists (about 9 bits/int): paper-layout chunks wider than
         # the shared-memory stage, read from global memory after an L2 prefetch
