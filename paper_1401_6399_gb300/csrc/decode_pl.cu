@@ -21,9 +21,11 @@
 //          (one width byte each) and checks the stream's size.
 //  decode  pl_tiles takes tiles of kTileChunks chunks of kChunk work units
 //          in ticket order, one chunk per warp.  A warp stages its chunk's
-//          blocks in shared memory with one bulk copy and sums their columns
-//          (one lane per block); the CTA publishes the tile's column sums,
-//          restarting at every list head.  The seed of a tile -- the column
+//          blocks in shared memory with one bulk copy (a chunk too wide for
+//          the stage is pulled into L2 instead and read from global memory)
+//          and sums their columns (one lane per block); the CTA publishes
+//          the tile's column sums, restarting at every list head.  The
+//          seed of a tile -- the column
 //          sums of its first list's earlier blocks (Section 5) -- comes from
 //          a decoupled look-back over the tiles before it, and the warps
 //          then unpack the staged blocks again (Algorithm 1, 4-lane
