@@ -1051,8 +1051,9 @@ def run_ours(args, rank, world, local):
     batch = api.ListBatch(encs, [n] * L, layout)
     # kernels of one bp_decode_batch call: GL the D4 kernel and the one for
     # other kinds (it leaves at once on D4 lists); PL plan, parse, resolve,
-    # emit, leftover, column sums, three scan kernels, two decode kernels, tail
-    launches_per_step = {capi.BP_LAYOUT_GPU: 2, capi.BP_LAYOUT_PAPER: 12,
+    # emit, leftover, four pl_tiles instances (D4 and other kinds, narrow and
+    # wide stage; the three not chosen leave at once), tail
+    launches_per_step = {capi.BP_LAYOUT_GPU: 2, capi.BP_LAYOUT_PAPER: 10,
                          capi.BP_LAYOUT_PFOR: 1}[layout]
     total_n = n * L
     out = torch.empty(total_n, dtype=torch.int32, device="cuda")

@@ -58,6 +58,7 @@ constexpr int kTileChunks = 7;           // chunk warps per CTA of pl_tiles (+ a
 constexpr int kTileThreads = 32 * (kTileChunks + 1);
 constexpr int kTileMinBlocks = 4;        // resident CTAs per SM for pl_tiles
 constexpr uint32_t kStageBytes = 3776;   // per warp and buffer: 32 blocks of average width <= 7.3
+constexpr uint32_t kStageWide = 5120;    // the same for wide lists (average width <= 9.9), 3 CTAs per SM
 constexpr uint64_t kOffMask = (1ull << 56) - 1;
 constexpr uint64_t kBadEntry = ~0ull;  // width byte 0xFF: no block to decode
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -88,7 +89,8 @@ struct PlScratch {
   uint32_t *seg_base;   // [count + 1] first segment of each list; [count]: total
   uint32_t *grp_base;   // [count + 1] first group of each list; [count]: total
   uint32_t *ctl;        // [0] nonzero: the lists do not tile the units, do nothing;
-                        // [1] nonzero: some list is not D4; [2] nonzero: some list is D4
+                        // [1] nonzero: some list is not D4; [2] nonzero: some list is D4;
+                        // [3] nonzero: the average chunk is wider than kStageBytes
   uint32_t *seg_in;     // [segs][kEnt] chain state entering the segment, by group entry
   uint32_t *live;       // [segs][kLiveCap] live line | successor distance << 16
   uint32_t *live_cnt;   // [segs]
@@ -214,8 +216,10 @@ __global__ void __launch_bounds__(1024)
   __shared__ uint64_t s_w[32][3];
   __shared__ uint64_t s_carry[3];
   __shared__ uint32_t s_bad, s_other, s_d4;
+  __shared__ unsigned long long s_enc;  // compressed bytes of all lists
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid == 0) {
+    s_enc = 0;
     s_carry[0] = s_carry[1] = s_carry[2] = 0;
     s_bad = 0;
     s_other = 0;
@@ -258,6 +262,7 @@ __global__ void __launch_bounds__(1024)
         s_d4 = 1;  // D4, or a bad header that the D4 passes report
       sc.seg_base[i] = (uint32_t)ex[1];
       sc.grp_base[i] = (uint32_t)ex[2];
+      atomicAdd(&s_enc, (unsigned long long)L.enc_bytes);
     }
     __syncthreads();
     if (tid == 0) {
@@ -275,6 +280,9 @@ __global__ void __launch_bounds__(1024)
     sc.ctl[0] = bad ? 1u : 0u;
     sc.ctl[1] = s_other;
     sc.ctl[2] = s_d4;
+    // pl_tiles with the wider stage runs when a chunk of kChunk units
+    // averages more bytes than the narrow stage holds
+    sc.ctl[3] = (uint64_t)kChunk * s_enc > (uint64_t)kStageBytes * total_units ? 1u : 0u;
     if (bad) set_status(status, BP_ERR_ARG);
   }
 }
@@ -954,8 +962,8 @@ struct Chunk {
 __device__ __forceinline__ bool stage_chunk(const uint8_t *data, const TileLists &src,
                                             const PlScratch &sc, uint64_t ch,
                                             uint64_t total_units, int lane, uint32_t bar,
-                                            uint32_t sbase, uint32_t &phase, Chunk &cx,
-                                            uint32_t *status) {
+                                            uint32_t sbase, uint32_t stage_bytes,
+                                            uint32_t &phase, Chunk &cx, uint32_t *status) {
   cx.u0 = ch * kChunk;
   cx.cnt = total_units - cx.u0 < kChunk ? (uint32_t)(total_units - cx.u0) : kChunk;
   cx.eL = (uint32_t)lane < cx.cnt ? sc.boffw[cx.u0 + lane] : kBadEntry;
@@ -975,7 +983,7 @@ __device__ __forceinline__ bool stage_chunk(const uint8_t *data, const TileLists
   if (m > 0 && fit) {
     const uint64_t st0 = __shfl_sync(kFull, offl, 0);
     const uint64_t bytes = __shfl_sync(kFull, offl + 16ull * bl, (int)m - 1) - st0;
-    if (bytes > 0 && bytes <= kStageBytes) {
+    if (bytes > 0 && bytes <= stage_bytes) {
       if (lane == 0) bulk_load(bar, sbase, data + L.enc_offset + st0, (uint32_t)bytes);
       const bool done = bulk_wait(bar, phase);
       phase ^= 1u;
@@ -1165,14 +1173,15 @@ __device__ __forceinline__ void chunk_units(const uint8_t *data, const TileLists
 // is read from memory once.  OTHER = false decodes the D4 lists, OTHER =
 // true the DM, D2 and D1 lists (launched after the first, leaving at once
 // if there are none); each runs its own tiles and look-back state.
-template <int MODE, bool OTHER>
-__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
+template <int MODE, bool OTHER, uint32_t STAGE>
+__global__ void __launch_bounds__(kTileThreads, STAGE > kStageBytes ? 3 : kTileMinBlocks)
     pl_tiles(const uint8_t *__restrict__ data, ListSrc src_in, uint64_t total_units,
              uint32_t *__restrict__ out, uint64_t *sums, PlScratch sc, uint32_t spin_limit,
              uint32_t *status) {
   if (sc.ctl[0] || (OTHER ? !sc.ctl[1] : !sc.ctl[2])) return;  // no list of this kind
+  if ((sc.ctl[3] != 0u) != (STAGE > kStageBytes)) return;      // the other stage size runs
   constexpr int kW = kTileChunks;  // chunk warps; warp kW is the control warp
-  __shared__ __align__(128) uint8_t s_stage[2][kW][kStageBytes];
+  __shared__ __align__(128) uint8_t s_stage[2][kW][STAGE];
   __shared__ bp_list s_lists[kListCache];
   __shared__ uint32_t s_kinds[kListCache];
   __shared__ __align__(8) uint64_t s_bar[2][kW];
@@ -1259,8 +1268,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks)
         const uint32_t sb = smem_addr(&s_stage[b][w][0]);
         Chunk cx;
         uint32_t ph = (parity >> b) & 1u;
-        ok = stage_chunk(data, src, sc, ch, total_units, lane, smem_addr(&s_bar[b][w]), sb, ph,
-                         cx, status);
+        ok = stage_chunk(data, src, sc, ch, total_units, lane, smem_addr(&s_bar[b][w]), sb, STAGE,
+                         ph, cx, status);
         parity = (parity & ~(1u << b)) | (ph << b);
         if (lane == 0) {
           s_u0[b][w] = cx.u0;
@@ -1416,25 +1425,27 @@ int launch_pl_decode(const uint8_t *data, const ListSrc &src, uint64_t total_uni
   pl_emit<<<8 * sms, kThreads, 0, s>>>(data, src, sc, status);
   pl_leftover<<<lgrid, kThreads, 0, s>>>(data, src, sc, out_cap, sums != nullptr, status);
   // persistent grids of resident CTAs; tiles are taken in ticket order
-  static int occ[4] = {-1, -1, -1, -1};
+  static int occ[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   auto grid = [&](int resident) {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(ntl, (uint64_t)resident));
   };
+  // D4 lists, then the other kinds; of each pair of stage sizes the one
+  // pl_plan did not choose leaves at once
+  auto tiles = [&](auto kernel, int &cache) {
+    kernel<<<grid(resident_grid(kernel, kTileThreads, cache)), kTileThreads, 0, s>>>(
+        data, src, total_units, out, sums, sc, spin_limit, status);
+  };
   if (sums) {
-    pl_tiles<kSum, false><<<grid(resident_grid(pl_tiles<kSum, false>, kTileThreads, occ[0])),
-                            kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc, spin_limit,
-                                              status);
-    pl_tiles<kSum, true><<<grid(resident_grid(pl_tiles<kSum, true>, kTileThreads, occ[1])),
-                           kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc, spin_limit,
-                                             status);
+    tiles(pl_tiles<kSum, false, kStageBytes>, occ[0]);
+    tiles(pl_tiles<kSum, false, kStageWide>, occ[1]);
+    tiles(pl_tiles<kSum, true, kStageBytes>, occ[2]);
+    tiles(pl_tiles<kSum, true, kStageWide>, occ[3]);
     pl_tail<true><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   } else {
-    pl_tiles<kStore, false><<<grid(resident_grid(pl_tiles<kStore, false>, kTileThreads, occ[2])),
-                              kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc,
-                                                spin_limit, status);
-    pl_tiles<kStore, true><<<grid(resident_grid(pl_tiles<kStore, true>, kTileThreads, occ[3])),
-                             kTileThreads, 0, s>>>(data, src, total_units, out, sums, sc, spin_limit,
-                                               status);
+    tiles(pl_tiles<kStore, false, kStageBytes>, occ[4]);
+    tiles(pl_tiles<kStore, false, kStageWide>, occ[5]);
+    tiles(pl_tiles<kStore, true, kStageBytes>, occ[6]);
+    tiles(pl_tiles<kStore, true, kStageWide>, occ[7]);
     pl_tail<false><<<lgrid, kThreads, 0, s>>>(data, src, out, sums, sc, status);
   }
   return cudaPeekAtLastError() == cudaSuccess ? BP_OK : BP_ERR_CUDA;
