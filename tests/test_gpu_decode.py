@@ -166,6 +166,34 @@ def test_decode_batch_mixed_kinds(orc, layout):
     assert batch.sums().tolist() == [int(x.astype(np.uint64).sum()) for x in xs]
 
 
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_paper_layout_stage_regimes(orc, kind):
+    """Paper layout at densities on both sides of its two shared-memory
+    stages (chunks of 32 blocks up to about 7.3 and 9.9 bits/int) and far
+    beyond them (chunks read from global memory after an L2 prefetch): each
+    list alone (its own density picks the stage), then all of them in one
+    batch (the average picks it, wider chunks go to global memory); decode
+    and decode+sum, bit-exact against the oracle and the input."""
+    n = 3 * 2048 * 16 + 2048 + 77  # many chunks and tiles, a ragged tail
+    xs, encs = [], []
+    for k, shift in enumerate((2, 3, 4, 5, 6, 9, 14)):  # about shift + 4 bits per integer
+        x = W.uniform(n, 0, n << shift, 0x5100 + 16 * kind + k)
+        enc = capi.bp_encode(x, capi.BP_LAYOUT_PAPER, delta=kind)
+        want = orc.pl_decode(enc.tobytes())
+        assert np.array_equal(want, x)
+        got = api.as_u32(api.decode(api.to_device(enc), capi.BP_LAYOUT_PAPER, n))
+        assert np.array_equal(got, want), (kind, shift)
+        assert api.decode_sum(api.to_device(enc), capi.BP_LAYOUT_PAPER, n) == \
+            int(x.astype(np.uint64).sum()) % (1 << 64)
+        xs.append(x)
+        encs.append(enc)
+    for order in (xs, xs[::-1]):
+        oe = encs if order is xs else encs[::-1]
+        batch = api.ListBatch(oe, [n] * len(oe), capi.BP_LAYOUT_PAPER)
+        assert np.array_equal(api.as_u32(batch.decode()), np.concatenate(order))
+        assert batch.sums().tolist() == [int(x.astype(np.uint64).sum()) for x in order]
+
+
 def _outlier_list(rng, n):
     """Sorted distinct values: small gaps with rare large jumps, so that
     S4-FastPFOR blocks carry exceptions of several widths."""
