@@ -846,12 +846,13 @@ __device__ __forceinline__ void staged_chunk(uint32_t pk, const BL &blocks, int 
 }
 
 
-// Column sums of a fully staged chunk, one lane per block.  Line k of a
-// block (16 bytes) holds word k of each of the 4 lane streams, and field i
-// of stream s is bits [b i, b i + b) of that stream (Section 4.2, Fig. 2):
-// lane j reads block j's lines in order through a window of three lines and
-// adds the 4 deltas of each field, one funnel shift each.  The width is a
-// run-time value: every lane runs the same 32 field steps.
+// Column sums of a full chunk (staged, or read from global memory), one
+// lane per block.  Line k of a block (16 bytes) holds word k of each of the
+// 4 lane streams, and field i of stream s is bits [b i, b i + b) of that
+// stream (Section 4.2, Fig. 2): lane j reads block j's lines in order
+// through a window of three lines and adds the 4 deltas of each field, one
+// funnel shift each.  The width is a run-time value: every lane runs the
+// same 32 field steps.
 struct LbWin {
   uint4 w0, w1, w2;  // lines kc, kc + 1 and kc + 2 (zeros past the block)
   uint32_t kc;
@@ -995,8 +996,8 @@ __device__ __forceinline__ bool stage_chunk(const uint8_t *data, const TileLists
       cx.staged = (uint32_t)m;
       cx.st0 = st0;
     } else if (bytes > 0 && m == kChunk) {
-      // too wide for the stage (average width above 7.3 bits): the fast
-      // paths read the blocks from global memory, pulled into L2 here
+      // too wide for this instance's stage: the fast paths read the
+      // blocks from global memory, pulled into L2 here
       if (lane == 0) bulk_prefetch_l2(data + L.enc_offset + st0, (uint32_t)bytes);
       cx.staged = kChunk;
       cx.st0 = st0;
